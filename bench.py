@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Benchmark: GB300 MGRIT on the PWM-driven annular machine, 18,240-DOF mesh, N = 4096.
+
+Workload (one "step" of this benchmark = one complete MGRIT solve to tolerance):
+  fine mesh: the 24 x 48 annulus refined twice (18,240 interior DOFs), linear
+  materials, three-phase triangle-carrier PWM at 20 kHz, J0 = 1e6 A/m^2,
+  T = 20 ms, N = 4096 backward-Euler steps; 3-level MGRIT, m = 16, FCF relaxation,
+  coarse time levels on the 1,104-DOF base mesh (direct spatial coarsening),
+  FP64 arithmetic form.  The MGRIT tolerance is chosen so that the maximal
+  relative L2 error per time point against GPU sequential stepping is <= 1e-6;
+  the error reached is reported.
+
+value = fine time steps resolved per second of MGRIT wall time (N / t_MGRIT),
+summed over ranks (independent replicas, one per GPU).  Also reported: GPU
+sequential stepping wall time on the same GB300 and the speedup, the live
+roofline of the dominant kernel (the batched step solve at 18,240 DOFs x 256
+columns), end-to-end throughput through the host-buffer entry point, sampled
+clocks, and the CPU oracle's sequential stepping on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MGRIT wall time vs GPU sequential stepping at <=1e-6 rel err; SpMM/CG HBM GB/s"
+UNIT = "time-steps/s"
+WORKLOAD = "cfg1: 18,240-DOF annulus, N=4096, T=20 ms, 3-level MGRIT m=16 FCF, coarse levels on 1,104 DOFs"
+N_STEPS, T_END, F_CARRIER = 4096, 20e-3, 20e3
+MGRIT_TOL = 1e-7  # relative C-point residual reduction; error vs sequential checked below
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=96, help="oracle steps timed for the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+def step_bytes_per_column_iteration(ns, W=7, nu=2, base_tile=16, krylov_bytes=8):
+    """Algorithmic bytes one column moves per PCG iteration of the batched step kernel.
+
+    ns: rows per multigrid depth (finest first).  Each vector pass counts once
+    (a gathered vector counts as one read), the ELL matrix (4-byte column index +
+    4-byte value per entry, 8-byte values for the FP64 operator) once per phase
+    for the whole launch, not per column, so it is added by the caller.
+    """
+    n0 = ns[0]
+    kb = krylov_bytes
+    b = 0.0
+    b += n0 * (4 + 4 * kb)  # A: z read, p, q read and written
+    b += n0 * 6 * kb  # B: x, p, r, q read; x, r written
+    nd = len(ns)
+    for d in range(nd - 1):
+        n, nc = ns[d], ns[d + 1]
+        rb = kb if d == 0 else 4
+        b += n * (rb + 8)  # first smoothing sweep: r read, x and s written
+        b += (nu - 1) * n * 16  # further sweeps: s, x read; x, s written
+        b += n * 4 + nc * 4  # restriction: s read, coarse r written
+        b += n * 12 + nc * 4  # prolongation: coarse x read, x read/written, y written
+        b += n * 12  # residual update: y read, s read/written
+        b += (nu - 1) * n * 16 + n * 12 + (n0 * kb if d == 0 else 0)  # post sweeps (+ r for (r, z))
+    nb = ns[-1]
+    b += nb * 8 + nb * nb * 4 / base_tile  # coarsest: r read, x written, dense inverse per tile
+    return b
+
+
+def matrix_bytes_per_iteration(ns, W=7, nu=2):
+    b = ns[0] * W * 12  # FP64 operator in phase A
+    for d in range(len(ns) - 1):
+        b += ns[d] * W * 8 * (nu + 1 + nu - 1)  # smoothing sweeps + residual update (FP32)
+    return b
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import synth
+    from synth.model import PwmSpec, machine_model
+    from paper_1912_03106_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as td
+
+        td.init_process_group("nccl", device_id=dev)
+    meshes = synth.mesh_hierarchy(3)
+    model = machine_model(pwm=PwmSpec(J0=1e6, f_carrier=F_CARRIER))
+    stream = torch.cuda.current_stream(local)
+    ctx = api.Context(local, stream)
+    ids = api.setup_machine(ctx, meshes, model)
+    n = ctx.mg_num_dofs(ids[2])
+    N, T = N_STEPS, T_END
+    opts = api.mgrit_opts(levels=3, m=(16, 16), space_level=(ids[2], ids[0], ids[0]), relax=1, tol=MGRIT_TOL,
+                          max_iter=60)
+    a0 = torch.zeros(n, dtype=torch.float64, device=dev)
+    out = torch.empty((N + 1, n), dtype=torch.float64, device=dev)
+    seq = torch.empty((N + 1, n), dtype=torch.float64, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as td
+
+            td.barrier()
+
+    # GPU sequential stepping (the baseline MGRIT is compared against), once
+    ctx.mg_sequential(ids[2], 64, T * 64 / N, a0, seq[:65])  # builds the operators
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, seq_st = ctx.mg_sequential(ids[2], N, T, a0, seq)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_s = e0.elapsed_time(e1) / 1e3
+
+    for _ in range(args.warmup):
+        ctx.mg_solve(N, T, a0, out, opts)
+    barrier()
+    # accuracy of the last warm-up solve against sequential stepping
+    diff = torch.linalg.vector_norm(out[1:] - seq[1:], dim=1) / torch.linalg.vector_norm(seq[1:], dim=1)
+    max_err = float(diff.max())
+
+    stats = []
+    with ClockSampler(local) as clocks:
+        barrier()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, st = ctx.mg_solve(N, T, a0, out, opts)
+            stats.append(st)
+        e1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+    dev_s = e0.elapsed_time(e1) / 1e3
+    t_step = dev_s / args.steps
+    if world > 1:
+        import torch.distributed as td
+
+        tt = torch.tensor([t_step], dtype=torch.float64, device=dev)
+        td.all_reduce(tt, op=td.ReduceOp.MAX)
+        t_step = float(tt)
+    value = world * N / t_step
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    a0_h = torch.zeros(n, dtype=torch.float64).pin_memory()
+    out_h = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
+    a0_np, out_np = a0_h.numpy(), out_h.numpy()
+    ctx.mg_solve_host(N, T, a0_np, out_np, opts)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.mg_solve_host(N, T, a0_np, out_np, opts)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_err = float(np.max(np.linalg.norm(out_np[1:] - seq[1:].cpu().numpy(), axis=1)
+                           / np.linalg.norm(seq[1:].cpu().numpy(), axis=1)))
+
+    roof = roofline(ctx, ids, seq, N, T, stream)
+
+    st = stats[-1]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dofs": n, "N": N, "T_s": T, "levels": 3, "m": [16, 16], "relax": "FCF",
+                   "space_levels": [n, ctx.mg_num_dofs(ids[0]), ctx.mg_num_dofs(ids[0])],
+                   "mgrit_tol_rel": MGRIT_TOL, "precond": "multigrid V(2,2), FP32, dense base inverse",
+                   "l2_flush": "inputs larger than L2 (600 MB trajectory per solve)",
+                   "parallelism": f"replicas x{world}"},
+        "mgrit": {"wall_s": t_step, "iters": st["iters"], "res_hist": st["res_hist"],
+                  "max_rel_err_vs_gpu_sequential": max_err, "step_solves": st["step_solves"],
+                  "batched_steps": st["batched_steps"], "pcg_iters": st["cg_iters"]},
+        "gpu_sequential": {"wall_s": seq_s, "time_steps_per_s": N / seq_s, "pcg_iters": seq_st["cg_iters"]},
+        "speedup_vs_gpu_sequential": seq_s / t_step,
+        "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 8,
+                "d2h_bytes_per_step": (N + 1) * n * 8, "max_rel_err_vs_gpu_sequential": e2e_err},
+        "roofline": roof,
+        "clocks": clocks.summary(),
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "wall_check_s": wall,
+    }
+    if rank == 0:
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as td
+
+        td.destroy_process_group()
+
+
+def roofline(ctx, ids, seq, N, T, stream):
+    """Time the dominant kernel (one batched FP64 step at 18,240 DOFs x 256 columns,
+    cold start, multigrid preconditioner) with CUDA events and relate its
+    algorithmic bytes to the measured HBM copy bandwidth."""
+    import torch
+
+    n = ctx.mg_num_dofs(ids[2])
+    k = 256
+    x_in = seq[0:N:16][:k].t().contiguous()  # C-point states as the columns
+    x_out = torch.zeros((n, k), dtype=torch.float64, device=x_in.device)
+    ctx.mg_step(ids[2], N, T, x_in, x_out, i0=1, istride=16)
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    iters = 0
+    for _ in range(reps):
+        _, st = ctx.mg_step(ids[2], N, T, x_in, x_out, i0=1, istride=16)
+        iters += st["cg_iters"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    it_per_col = iters / reps / k
+    ns = [n, ctx.mg_num_dofs(ids[1]), ctx.mg_num_dofs(ids[0])]
+    per_col = step_bytes_per_column_iteration(ns)
+    mat = matrix_bytes_per_iteration(ns)
+    bytes_launch = it_per_col * (k * per_col + mat) + k * n * 8 * 9
+    peak = None
+    src = "fallback"
+    try:
+        peak = json.load(open(PEAKS_FILE))["hbm_gbs"]
+        src = "measured"
+    except (OSError, KeyError, ValueError):
+        peak = 6800.0
+    achieved = bytes_launch / t / 1e9
+    return {"bound": "hbm", "kernel": "k_phi_batch<16> (18,240 DOFs x 256 columns, FP64 form)",
+            "achieved": achieved, "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "launch_ms": t * 1e3, "pcg_iters_per_column": it_per_col,
+            "algorithmic_bytes_per_launch": bytes_launch}
+
+
+def cpu_baseline(args):
+    """The oracle's sequential stepping (banded Cholesky, FP64) on a bounded sample."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "import numpy as np, synth\n"
+        "from synth.model import PwmSpec, machine_model\n"
+        "from oracle.problem import MachineProblem\n"
+        "from oracle import stepper\n"
+        "ms = synth.mesh_hierarchy(3)\n"
+        "P = MachineProblem(ms, machine_model(pwm=PwmSpec(J0=1e6, f_carrier=%r)), %d, %r, (2,), ())\n"
+        "phi = P.levels[0].phi\n"
+        "u = np.zeros(P.n); t = time.perf_counter()\n"
+        "for i in range(1, %d + 1): u = phi(u, i)\n"
+        "dt = time.perf_counter() - t\n"
+        "print(json.dumps({'steps': %d, 'seconds': dt}))\n"
+    ) % (ROOT, F_CARRIER, N_STEPS, T_END, args.cpu_sample, args.cpu_sample)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        res = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": res["steps"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"first {res['steps']} of {N_STEPS} backward-Euler steps of the 18,240-DOF model, "
+                          "sequential, banded Cholesky factored once (factorisation not timed)"}
+    except Exception as e:  # pragma: no cover
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import synth
+    from synth.model import PwmSpec, machine_model
+    from oracle.problem import MachineProblem
+
+    ms = synth.mesh_hierarchy(3)
+    P = MachineProblem(ms, machine_model(pwm=PwmSpec(J0=1e6, f_carrier=F_CARRIER)), N_STEPS, T_END, (2,), ())
+    phi = P.levels[0].phi
+    sample = 32
+
+    def step():
+        u = np.zeros(P.n)
+        t = time.perf_counter()
+        for i in range(1, sample + 1):
+            u = phi(u, i)
+        return time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        step()
+    times = [step() for _ in range(args.steps)]
+    t_step = sum(times) / len(times)
+    value = sample / t_step
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} sequential backward-Euler steps of the 18,240-DOF model per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

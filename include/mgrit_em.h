@@ -1,0 +1,215 @@
+/*
+ * mgrit_em.h -- C ABI of the GB300 MGRIT eddy-current library (libmgrit_em.so).
+ *
+ * The library solves the semi-discrete 2D eddy-current problem
+ *     M a'(t) + K(a) a = f(t),   f(t) = J0 * sum_s b_s(t) F_s          (Sec. 3.1,
+ *                                                   Eq. semi_discrete_system)
+ * on P1 triangle meshes, with backward Euler (Eq. discrete_system) as the
+ * one-step propagator Phi (Sec. 2, Eq. mgrit_nonlinear_system), either
+ * sequentially (forward block solve of the block-bidiagonal space-time system,
+ * Sec. 2) or by FAS-MGRIT (Algorithm 1, Sec. 2.1) with F/FCF relaxation,
+ * injection in time, ideal interpolation, and spatial coarsening between
+ * nested meshes (Sec. 2.2, Sec. 3.4).  b_s(t) is the three-phase PWM switching
+ * function (Sec. 3.2-3.3, Eqs. machine_pwm, machine_reference_signal,
+ * machine_carrier_signal).
+ *
+ * Conventions
+ *  - Every call returns mg_status; no C++ exception crosses the ABI.  On error
+ *    mg_last_error() holds a message (valid until the next call on that context).
+ *  - Set-up calls take HOST arrays and copy them; the caller keeps ownership.
+ *  - Solve calls take DEVICE pointers (e.g. torch CUDA tensors) unless the
+ *    function name ends in _host.  The library never frees caller memory.
+ *  - Vectors of one mesh level hold its interior nodes (Dirichlet A_z = 0 nodes
+ *    removed) in increasing node order.  A trajectory is time-major:
+ *    out[i * n + j] = a_j(t_i), i = 0..N.  A batch of k vectors is node-major:
+ *    x[j * ld + c] is node j of column c (ld >= k).
+ *  - Work is enqueued on the context's stream; calls that return statistics
+ *    synchronise that stream.
+ *  - Invalid arguments are rejected with MG_EINVAL before any launch.
+ *  - Solver failures (CG or Newton not converged, MGRIT max iterations) are
+ *    reported as a status; the outputs then hold the last iterate.
+ *  - Every device wait inside the library's kernels is bounded; a wait that
+ *    runs out returns MG_ETIMEOUT instead of hanging.
+ */
+#ifndef MGRIT_EM_H
+#define MGRIT_EM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+
+typedef enum {
+    MG_OK = 0,
+    MG_EINVAL = -1,        /* bad argument, size or index                       */
+    MG_ENOMEM = -2,        /* device or host allocation failed                  */
+    MG_ECUDA = -3,         /* a CUDA runtime call failed                        */
+    MG_ENOTSPD = -4,       /* an assembled operator is not SPD (non-positive pivot) */
+    MG_ECG_MAXIT = -5,     /* a linear solve hit its iteration limit            */
+    MG_ENEWTON = -6,       /* Newton did not converge (Sec. 5: poor initial guess) */
+    MG_EMGRIT_MAXIT = -7,  /* MGRIT reached max_iter before the tolerance       */
+    MG_ETIMEOUT = -8,      /* a bounded device wait ran out                     */
+    MG_ESTATE = -9         /* call order violated (e.g. solve before set-up)    */
+} mg_status;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`; work goes to `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream). */
+mg_status mg_create(mg_ctx** out, int device, void* cuda_stream);
+void mg_destroy(mg_ctx* ctx);
+const char* mg_last_error(const mg_ctx* ctx);
+mg_status mg_set_stream(mg_ctx* ctx, void* cuda_stream);
+
+/* ------------------------------------------------------------------- set-up */
+
+/* Add a P1 triangle mesh (Sec. 3.4).  xy: 2*n_nodes doubles (x, y per node);
+ * tri: 3*n_tri node ids, counter-clockwise; region: n_tri tags in [0, 64);
+ * dir_nodes: the n_dir nodes with A_z = 0 (the other nodes are the unknowns).
+ * *level_out receives the mesh level id (0, 1, ... in call order). */
+mg_status mg_add_mesh(mg_ctx* ctx, int* level_out, int64_t n_nodes, const double* xy,
+                      int64_t n_tri, const int32_t* tri, const int32_t* region,
+                      int64_t n_dir, const int32_t* dir_nodes);
+
+/* Nested refinement between two added meshes (Sec. 3.4: FE nodal interpolation
+ * as grid transfer).  parent: 2 * n_nodes(fine) coarse node ids; a fine node
+ * with equal parents coincides with that coarse node, otherwise it is the
+ * midpoint of the coarse edge (p0, p1).  Defines P_s (fine <- coarse) between
+ * the two levels; transfers across several refinements are composed. */
+mg_status mg_add_refinement(mg_ctx* ctx, int fine_level, int coarse_level, const int32_t* parent);
+
+/* Material of a region tag (Sec. 3.1; Sec. 5 for the Brauer law):
+ * law 0: nu constant; law 1: nu(|B|^2) = k1 exp(k2 |B|^2) + k3 (nu unused). */
+mg_status mg_set_material(mg_ctx* ctx, int32_t region, double sigma, double nu, int law,
+                          double k1, double k2, double k3);
+
+/* Region `region` carries J_s = sign * J0 * b_phase(t) (phase 0..2, sign +-1). */
+mg_status mg_set_source(mg_ctx* ctx, int32_t region, int phase, int sign);
+
+/* PWM source (Sec. 3.2-3.3): b_s = sgn(r_s - c), sgn(0) = 0,
+ * r_s = mod_index sin(2 pi f_ref t + phi_s), phi = (0, -2pi/3, -4pi/3);
+ * carrier 0: sawtooth 2 frac(f_c t) - 1 (Eq. machine_carrier_signal);
+ * carrier 1: triangle 1 - 4 |frac(f_c t) - 1/2|.  t_i = i T / N; when f_c T is
+ * an integer the carrier phase is formed exactly from integers. */
+mg_status mg_set_pwm(mg_ctx* ctx, double J0, double f_ref, double f_carrier, int carrier,
+                     double mod_index);
+
+/* Assemble all meshes (P1 stiffness, consistent mass, phase loads) on the device.
+ * Called implicitly by the first solve; returns MG_ENOTSPD if an operator has a
+ * non-positive diagonal. */
+mg_status mg_finalize(mg_ctx* ctx);
+
+/* Number of unknowns (interior nodes) of a mesh level, or -1. */
+int64_t mg_num_dofs(const mg_ctx* ctx, int level);
+
+/* Copy the assembled operators of a level to HOST buffers (for inspection):
+ * rowptr[n+1] (int64), col[nnz] (int32), K[nnz], M[nnz] (double) and
+ * F[3*n] (phase-major).  Pass NULL for any output to skip it; *nnz_out
+ * receives the number of stored entries. */
+mg_status mg_get_operators(mg_ctx* ctx, int level, int64_t* nnz_out, int64_t* rowptr,
+                           int32_t* col, double* K, double* M, double* F);
+
+/* PWM table of the fine grid t_i = i T / N, i = 0..N, into HOST out[3*(N+1)]
+ * (row i holds b_1, b_2, b_3 of t_i), computed by the library's kernel. */
+mg_status mg_pwm_table(mg_ctx* ctx, int64_t N, double T, int8_t* out);
+
+/* ---------------------------------------------------------------- solving */
+
+typedef enum { MG_FP64 = 0, MG_FP32_REFINE = 1 } mg_precision;
+
+typedef enum { MG_PRECOND_JACOBI = 0, MG_PRECOND_MULTIGRID = 1 } mg_precond;
+
+typedef struct {
+    /* linear solver of one backward-Euler step: batched PCG, preconditioned by
+     * one FP32 geometric-multigrid V-cycle over the nested meshes (coarsest mesh
+     * solved by a dense inverse) or by Jacobi */
+    double cg_tol;      /* FP64 mode: stop at ||b - L x|| <= cg_tol ||b|| per column      */
+    double refine_tol;  /* FP32+refinement: outer FP64 stop ||b - L x|| <= refine_tol ||b|| */
+    double inner_tol;   /* FP32+refinement: inner FP32 PCG relative reduction per sweep    */
+    int max_cg;         /* iteration limit of one (inner) PCG                              */
+    int max_refine;     /* FP32+refinement: limit of outer sweeps                          */
+    int precision;      /* mg_precision                                                    */
+    int cluster;        /* CTAs per cluster (1..8), 0 = library choice                     */
+    int tile;           /* columns per cluster (1, 8, 16, 32), 0 = library choice          */
+    int precond;        /* mg_precond                                                      */
+    int smooth;         /* damped-Jacobi sweeps before and after each coarse correction    */
+    double omega;       /* Jacobi damping factor                                           */
+} mg_solver_opts;
+
+/* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,
+ * inner_tol 1e-5, max_cg 2000, max_refine 30, FP64, multigrid with 2 sweeps
+ * of damping 0.7). */
+void mg_solver_defaults(mg_solver_opts* opts);
+
+typedef struct {
+    int iters;                /* MGRIT iterations (coarse-grid corrections)        */
+    int n_hist;               /* entries of res_hist                               */
+    double res_hist[64];      /* fine-level C-point residual norm after each relaxation */
+    double t_setup, t_solve;  /* seconds (host clock around synchronised phases)   */
+    int64_t step_solves;      /* column-steps solved (one Phi application each)    */
+    int64_t batched_steps;    /* Phi launches (each over one batch of columns)     */
+    int64_t cg_iters;         /* PCG iterations summed over columns (FP32+refinement:
+                                 per column tile, the inner iterations of its slowest column) */
+    int32_t worst_status;     /* worst per-column solver status seen               */
+    int64_t launches;         /* CUDA kernels the call launched                    */
+} mg_stats;
+
+/* One batched backward-Euler step on mesh `level` (Eq. discrete_system):
+ * for each column c < k, x_out[:, c] solves
+ *     (M/dt + K) x = (M/dt) x_in[:, c] + J0 sum_s b_s(t_{i_c}) F_s,
+ * with dt = dt_mult * T / N and fine time index i_c = i0 + c * istride
+ * (0 <= i_c <= N).  x_out also serves as the initial guess when guess != 0.
+ * Node-major layouts with leading dimensions ld_in, ld_out >= k.
+ * stats may be NULL (then the call does not synchronise). */
+mg_status mg_step(mg_ctx* ctx, int level, int64_t N, double T, int64_t dt_mult, int k,
+                  int64_t i0, int64_t istride, const double* x_in, int64_t ld_in,
+                  double* x_out, int64_t ld_out, int guess, const mg_solver_opts* opts,
+                  mg_stats* stats);
+
+/* Sequential time stepping (forward block solve, Sec. 2): out[0] = a0,
+ * out[i] = Phi_i(out[i-1]), i = 1..N, on mesh `level` with dt = T/N.
+ * a0: n doubles; out: (N+1)*n doubles, time-major (device pointers). */
+mg_status mg_sequential(mg_ctx* ctx, int level, int64_t N, double T, const double* a0,
+                        double* out, const mg_solver_opts* opts, mg_stats* stats);
+
+typedef struct {
+    int levels;            /* time levels L >= 1 (1 = sequential solve)                  */
+    int m[8];              /* coarsening factor from level l to l+1, l < L-1             */
+    int space_level[8];    /* mesh level used on each time level (spatial coarsening)   */
+    int relax;             /* 0: F-relaxation, 1: FCF-relaxation (gamma of Algorithm 1) */
+    double tol;            /* stop when ||r|| <= tol (x ||r_0|| if tol_relative)         */
+    int tol_relative;
+    int max_iter;
+    int restrict_mode;     /* residual R_s: 0 injection, 1 P^T, 2 diag(P^T 1)^-1 P^T      */
+    mg_solver_opts solver;
+} mg_opts;
+
+/* Fill opts with defaults: 2 levels, m = 16, FCF, tol 1e-10 relative,
+ * max_iter 50, restrict_mode 2, mg_solver_defaults(). */
+void mg_opts_defaults(mg_opts* opts);
+
+/* FAS-MGRIT (Algorithm 1 with recursive V-cycles) for A u = g, g = (a0, 0, ..., 0)
+ * on time level 0 with N steps of T/N on mesh opts->space_level[0].
+ * N must be divisible by m[0] * ... * m[L-2].  a0: n doubles; out: (N+1)*n
+ * doubles, time-major (device pointers).  Iterate: relax (F or FCF), C-point
+ * residual norm, stop test, coarse-grid correction.  Returns MG_EMGRIT_MAXIT if
+ * the tolerance was not reached (out holds the last iterate). */
+mg_status mg_solve(mg_ctx* ctx, int64_t N, double T, const double* a0, double* out,
+                   const mg_opts* opts, mg_stats* stats);
+
+/* As mg_solve / mg_sequential with HOST a0 and out: the call copies a0 to the
+ * device, solves, and copies the trajectory back (both copies on the stream). */
+mg_status mg_solve_host(mg_ctx* ctx, int64_t N, double T, const double* a0_host,
+                        double* out_host, const mg_opts* opts, mg_stats* stats);
+mg_status mg_sequential_host(mg_ctx* ctx, int level, int64_t N, double T,
+                             const double* a0_host, double* out_host,
+                             const mg_solver_opts* opts, mg_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGRIT_EM_H */

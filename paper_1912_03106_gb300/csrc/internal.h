@@ -1,0 +1,185 @@
+// Internal state of libmgrit_em.so (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mgrit_em.h"
+
+#define MG_MAX_REGIONS 64
+
+struct MgError {
+    mg_status st;
+    std::string msg;
+};
+
+// Throw from host code inside the library; every ABI entry point catches.
+[[noreturn]] void mg_fail(mg_status st, const std::string& msg);
+void mg_check_cuda(cudaError_t e, const char* what);
+#define MG_CUDA(call) mg_check_cuda((call), #call)
+
+// Device buffer owned by the context.
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void release();
+    void ensure(size_t nbytes);  // grow (contents not kept)
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <class T>
+void upload(DBuf& b, const std::vector<T>& v) {
+    b.ensure(v.size() * sizeof(T));
+    if (!v.empty()) MG_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+struct Material {
+    double sigma = 0.0, nu = 0.0;
+    int law = 0;
+    double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+    bool set = false;
+};
+
+struct Source {
+    int phase = -1, sign = 0;
+};
+
+struct PwmSpec {
+    double J0 = 0.0, f_ref = 50.0, f_carrier = 5e3, mod_index = 1.0;
+    int carrier = 1;
+    bool set = false;
+};
+
+// One P1 mesh and its assembled linear operators (interior unknowns only).
+struct MeshLevel {
+    int64_t n_nodes = 0, n_tri = 0, n = 0, nnz = 0;
+    std::vector<double> xy;
+    std::vector<int32_t> tri, region;
+    std::vector<int32_t> node2dof;  // -1 on Dirichlet nodes
+    std::vector<int32_t> dof2node;
+    // CSR pattern of the interior block (host copies)
+    std::vector<int32_t> rowptr_h, col_h, diag_h;
+    // device data
+    DBuf rowptr, col, diag;     // int32
+    DBuf tri_d, xy_d;           // int32 / double
+    DBuf slot_ptr, slot_src;    // slot -> element-local contributions (elem * 9 + a * 3 + b)
+    DBuf load_ptr, load_src;    // dof -> element-local vertex contributions (elem * 3 + a)
+    DBuf elem_sigma, elem_nu, elem_law, elem_k, elem_phase;  // per-element material data
+    DBuf area, grad;            // |T| and barycentric gradients (6 per element)
+    DBuf elemK, elemM;          // 9 values per element
+    DBuf K, M, F;               // nnz, nnz, 3 * n (double)
+    // ELL view of the CSR pattern: width W, column-major (entry w of row i at w * n + i);
+    // padding entries point at the row itself with slot -1
+    int ell_W = 0;
+    DBuf ell_col, ell_slot;     // int32 W x n
+    // one refinement step to the coarse parent mesh (if any): P with <= 2 entries per fine row
+    int parent_mesh = -1;
+    DBuf par, pw;               // int32 2 x n coarse dofs (-1: none), float 2 x n weights
+    int rt_W = 0;
+    DBuf rt_col, rt_w;          // P^T as ELL (rt_W x n_parent, column-major) over the parent's dofs
+    bool assembled = false;
+};
+
+// One level of the multigrid hierarchy of a step operator (same dt on every level).
+struct MgDepth {
+    int mesh = 0;
+    int64_t n = 0;
+    int W = 0;
+    DBuf L64, M64, L32, LD32, dinv64, dinv32;  // ELL values (W x n) and Jacobi data
+};
+
+// L = M / dt + K on one mesh level and its multigrid hierarchy: depth 0 is the
+// level itself, depth d+1 the parent mesh of depth d, the last depth the base mesh
+// (no parent), solved by the dense inverse `base_inv` (FP32, n x n row-major).
+struct StepOp {
+    int mesh = 0;
+    double dt = 0.0;
+    std::vector<MgDepth*> mg;
+    DBuf base_inv;
+    ~StepOp() { for (auto* d : mg) delete d; }
+};
+
+// P_s between two mesh levels (composed over refinements), interior DOFs.
+struct Transfer {
+    int fine = -1, coarse = -1;
+    int64_t nf = 0, nc = 0;
+    DBuf P_ptr, P_col, P_val;    // CSR n_f x n_c
+    DBuf PT_ptr, PT_col, PT_val; // CSR n_c x n_f
+    DBuf inj;                    // n_c: fine dof at each coarse dof's node
+    DBuf PT_rowsum_inv;          // n_c: 1 / (P^T 1)
+};
+
+struct mg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    std::vector<MeshLevel> meshes;
+    std::vector<std::pair<std::pair<int, int>, std::vector<int32_t>>> refinements;  // (fine, coarse) -> parent
+    Material mats[MG_MAX_REGIONS];
+    Source srcs[MG_MAX_REGIONS];
+    PwmSpec pwm;
+    bool finalized = false;
+    std::vector<StepOp*> ops;
+    std::map<std::pair<int, int>, Transfer*> transfers;
+    // PWM table cache
+    DBuf pwm_table;
+    int64_t pwm_N = -1;
+    double pwm_T = 0.0;
+    // reusable workspaces
+    DBuf ws[32];       // step-solver work vectors
+    DBuf host_in, host_out;  // staging of the *_host entry points
+    DBuf counters;     // device: [u64 PCG iteration sum][i32 worst status]
+    DBuf flag;         // int32 error flag
+    DBuf solve_buf[16];  // MGRIT level storage
+    ~mg_ctx();
+};
+
+#define MG_MAX_DEPTH 6
+#define MG_MAX_DENSE 4096   // largest base mesh inverted densely
+
+// ---- set-up helpers (setup.cu)
+void ctx_finalize(mg_ctx* c);
+StepOp& ctx_step_op(mg_ctx* c, int mesh, double dt);
+Transfer& ctx_transfer(mg_ctx* c, int fine, int coarse);
+const int8_t* ctx_pwm_table(mg_ctx* c, int64_t N, double T);
+
+// ---- batched backward-Euler step (pcg.cu)
+struct PhiIO {
+    int k = 0;
+    const double* xprev = nullptr;
+    int64_t ld_prev = 0;
+    const double* g = nullptr;  // added after the solve (FAS right-hand side), may be null
+    int64_t ld_g = 0;
+    const double* guess = nullptr;  // initial guess of Phi(xprev) + g, may be null
+    int64_t ld_guess = 0;
+    double* xout = nullptr;
+    int64_t ld_out = 0;
+    const int8_t* signs = nullptr;  // (N+1) x 3 PWM table of the fine grid
+    int64_t t0 = 0, tstride = 0;    // fine time index of column c: t0 + c * tstride
+};
+
+struct SolveCounters {
+    int64_t step_solves = 0, batched_steps = 0, cg_iters = 0, launches = 0;
+    int32_t worst_status = 0;
+};
+
+// Enqueue one batched step (no synchronisation).  PCG iteration totals and the
+// worst per-column status accumulate in ctx->counters on the device;
+// `counters` (host, may be null) counts launches and column-steps.
+void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so,
+               SolveCounters* counters);

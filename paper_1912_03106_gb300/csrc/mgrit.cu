@@ -1,0 +1,667 @@
+// FAS-MGRIT driver (Algorithm 1, Sec. 2.1-2.2) and sequential stepping (Sec. 2).
+//
+// Storage of one non-coarsest time level l with N_l intervals and factor m:
+// m "slabs", slab j holding the points t = c*m + j (c = 0..N_l/m) as the columns
+// of a node-major n_l x ld matrix (ld >= N_l/m + 1).  F-relaxation step j then
+// reads slab j-1 and writes slab j, C-relaxation reads slab m-1 and writes slab 0
+// shifted by one column: every batched step works on unit-stride columns.  The
+// coarsest level stores its points time-major and is solved sequentially.
+//
+// One iteration on level l (relaxation, C-point residual r_c = g_cm - u_cm +
+// Phi(u_cm-1), restriction by injection in time and R_s in space, FAS right-hand
+// side G = A_2(u2) + g2, recursive coarse solve, correction u_cm += P_s(v - u2)
+// and, below the finest level, the F-relaxation that completes ideal
+// interpolation) follows Algorithm 1; on the finest level that F-relaxation is
+// the first step of the next iteration's relaxation, which computes the same
+// values.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Address of (time point t, node i) of a level store.
+struct LevelView {
+    double* base;
+    int64_t n, m, ld, slab;  // m == 0: time-major
+    __host__ __device__ int64_t idx(int64_t t, int64_t i) const {
+        if (m == 0) return t * n + i;
+        return (t % m) * slab + i * ld + t / m;
+    }
+};
+
+// r[i][c] = g(cm) - u(cm) + V[i][c-1] for c >= 1, r[i][0] = 0; partial sums of r^2.
+__global__ void k_cpoint_residual(int64_t n, int64_t NT, const double* __restrict__ U0, const double* __restrict__ G0,
+                                  int64_t ld, const double* __restrict__ V, int64_t ldv, double* __restrict__ R,
+                                  int64_t ldr, double* __restrict__ partial) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    const int64_t total = n * (NT + 1);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / (NT + 1), c = q % (NT + 1);
+        double r = 0.0;
+        if (c > 0) {
+            r = V[i * ldv + c - 1] - U0[i * ld + c];
+            if (G0) r += G0[i * ld + c];
+        }
+        R[i * ldr + c] = r;
+        acc += r * r;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) acc += partial[q];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// Restriction (Algorithm 1, lines 4-5): W[:, c] = R_s u(cm) (injection at coarse
+// nodes), g2[:, c] = R_s r_c with mode 0 injection, 1 P^T, 2 diag(P^T 1)^-1 P^T.
+__global__ void k_restrict(int64_t nc, int64_t NT, const double* __restrict__ U0, int64_t ld,
+                           const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ inj,
+                           const int32_t* __restrict__ pt_ptr, const int32_t* __restrict__ pt_col,
+                           const double* __restrict__ pt_val, const double* __restrict__ rinv, int mode,
+                           double* __restrict__ W, double* __restrict__ g2, int64_t ldw) {
+    const int64_t total = nc * (NT + 1);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ic = q / (NT + 1), c = q % (NT + 1);
+        int64_t src = inj ? inj[ic] : ic;
+        W[ic * ldw + c] = U0[src * ld + c];
+        double gv;
+        if (!inj || mode == 0) {
+            gv = R[src * ldr + c];
+        } else {
+            gv = 0.0;
+            for (int32_t e = pt_ptr[ic]; e < pt_ptr[ic + 1]; ++e) gv += pt_val[e] * R[(int64_t)pt_col[e] * ldr + c];
+            if (mode == 2) gv *= rinv[ic];
+        }
+        g2[ic * ldw + c] = gv;
+    }
+}
+
+// FAS right-hand side of the coarse level (Algorithm 1, line 6):
+// G_0 = u2_0 + g2_0, G_c = u2_c - Phi_c(u2_{c-1}) + g2_c; coarse iterate v = u2.
+__global__ void k_fas_rhs(int64_t nc, int64_t Nc, const double* __restrict__ W, const double* __restrict__ g2,
+                          const double* __restrict__ Vc, int64_t ldw, LevelView Gv, LevelView Uv) {
+    const int64_t total = nc * (Nc + 1);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / (Nc + 1), t = q % (Nc + 1);
+        double w = W[i * ldw + t];
+        double gval = w + g2[i * ldw + t];
+        if (t > 0) gval -= Vc[i * ldw + t - 1];
+        Gv.base[Gv.idx(t, i)] = gval;
+        Uv.base[Uv.idx(t, i)] = w;
+    }
+}
+
+// Correction (Algorithm 1, lines 7-9): u(cm) += P_s (v_c - u2_c), c = 1..NT.
+__global__ void k_correct(int64_t nf, int64_t NT, double* __restrict__ U0, int64_t ld, LevelView Vv,
+                          const double* __restrict__ W, int64_t ldw, const int32_t* __restrict__ p_ptr,
+                          const int32_t* __restrict__ p_col, const double* __restrict__ p_val) {
+    const int64_t total = nf * NT;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / NT, c = q % NT + 1;
+        double e;
+        if (p_ptr) {
+            e = 0.0;
+            for (int32_t k = p_ptr[i]; k < p_ptr[i + 1]; ++k) {
+                int64_t j = p_col[k];
+                e += p_val[k] * (Vv.base[Vv.idx(c, j)] - W[j * ldw + c]);
+            }
+        } else {
+            e = Vv.base[Vv.idx(c, i)] - W[i * ldw + c];
+        }
+        U0[i * ld + c] += e;
+    }
+}
+
+// Level store -> time-major trajectory.
+__global__ void k_to_time_major(int64_t n, int64_t N, LevelView Uv, double* __restrict__ out) {
+    const int64_t total = n * (N + 1);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t t = q / n, i = q % n;
+        out[q] = Uv.base[Uv.idx(t, i)];
+    }
+}
+
+__global__ void k_fill_column(int64_t n, const double* __restrict__ src, double* __restrict__ dst, int64_t ld) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i * ld] = src[i];
+}
+
+struct Level {
+    int mesh = 0;
+    int64_t n = 0, N = 0, m = 0, NT = 0, ld = 0, stride = 1;
+    double dt = 0.0;
+    StepOp* op = nullptr;
+    Transfer* tr = nullptr;  // to the next level (null if the same mesh)
+    double *U = nullptr, *G = nullptr;     // iterate and FAS right-hand side (G null on level 0)
+    double *R = nullptr, *V = nullptr;     // C-point residual and Phi(u_cm-1) (n x ld)
+    double *W = nullptr, *g2 = nullptr, *Vc = nullptr;  // restricted state / residual / coarse Phi (this level's mesh)
+    int64_t ldw = 0;
+    LevelView view() const { return LevelView{U, n, m, ld, n * ld}; }
+    LevelView gview() const { return LevelView{G, n, m, ld, n * ld}; }
+};
+
+struct Solver {
+    mg_ctx* c;
+    int64_t N;
+    double T;
+    mg_opts o;
+    std::vector<Level> lv;
+    const int8_t* signs = nullptr;
+    SolveCounters cnt;
+    double* partial = nullptr;
+    double* norm = nullptr;
+    static constexpr int kRedBlocks = 304;
+
+    void phi(int l, int k, const double* xprev, int64_t ldp, double* xout, int64_t ldo, const double* g,
+             int64_t ldg, int64_t t0, int64_t tstride) {
+        PhiIO io;
+        io.k = k;
+        io.xprev = xprev;
+        io.ld_prev = ldp;
+        io.g = g;
+        io.ld_g = ldg;
+        io.guess = xout;  // warm start from the current iterate
+        io.ld_guess = ldo;
+        io.xout = xout;
+        io.ld_out = ldo;
+        io.signs = signs;
+        io.t0 = t0;
+        io.tstride = tstride;
+        phi_batch(c, *lv[l].op, io, o.solver, &cnt);
+    }
+
+    // F-relaxation: u(cm+j) = Phi(u(cm+j-1)) + g(cm+j), j = 1..m-1, all intervals at once.
+    void f_relax(int l) {
+        Level& L = lv[l];
+        const int64_t slab = L.n * L.ld;
+        for (int64_t j = 1; j < L.m; ++j)
+            phi(l, (int)L.NT, L.U + (j - 1) * slab, L.ld, L.U + j * slab, L.ld, L.G ? L.G + j * slab : nullptr, L.ld,
+                j * L.stride, L.m * L.stride);
+    }
+
+    // C-relaxation: u(cm) = Phi(u(cm-1)) + g(cm), c = 1..NT.
+    void c_relax(int l) {
+        Level& L = lv[l];
+        const int64_t slab = L.n * L.ld;
+        phi(l, (int)L.NT, L.U + (L.m - 1) * slab, L.ld, L.U + 1, L.ld, L.G ? L.G + 1 : nullptr, L.ld,
+            L.m * L.stride, L.m * L.stride);
+    }
+
+    void relax(int l) {
+        f_relax(l);
+        for (int q = 0; q < o.relax; ++q) {
+            c_relax(l);
+            f_relax(l);
+        }
+    }
+
+    // r_c for c = 0..NT into L.R; if want_norm, the squared norm into norm[0].
+    void residual(int l) {
+        Level& L = lv[l];
+        const int64_t slab = L.n * L.ld;
+        PhiIO io;
+        io.k = (int)L.NT;
+        io.xprev = L.U + (L.m - 1) * slab;
+        io.ld_prev = L.ld;
+        io.guess = L.U + 1;  // Phi(u(cm-1)) is close to u(cm)
+        io.ld_guess = L.ld;
+        io.xout = L.V;
+        io.ld_out = L.ld;
+        io.signs = signs;
+        io.t0 = L.m * L.stride;
+        io.tstride = L.m * L.stride;
+        phi_batch(c, *L.op, io, o.solver, &cnt);
+        k_cpoint_residual<<<kRedBlocks, 256, 0, c->stream>>>(L.n, L.NT, L.U, L.G, L.ld, L.V, L.ld, L.R, L.ld, partial);
+        k_sum_partials<<<1, 256, 0, c->stream>>>(kRedBlocks, partial, norm);
+        cnt.launches += 2;
+        MG_CUDA(cudaGetLastError());
+    }
+
+    void sequential_level(int l) {
+        Level& L = lv[l];
+        for (int64_t t = 1; t <= L.N; ++t)
+            phi(l, 1, L.U + (t - 1) * L.n, 1, L.U + t * L.n, 1, L.G + t * L.n, 1, t * L.stride, 0);
+    }
+
+    void coarse_correction(int l) {
+        Level& F = lv[l];
+        Level& C = lv[l + 1];
+        // restriction into the coarse mesh's node-major W, g2 (columns = coarse points)
+        const Transfer* tr = F.tr;
+        k_restrict<<<nblk(C.n * (F.NT + 1)), 256, 0, c->stream>>>(
+            C.n, F.NT, F.U, F.ld, F.R, F.ld, tr ? tr->inj.as<int32_t>() : nullptr,
+            tr ? tr->PT_ptr.as<int32_t>() : nullptr, tr ? tr->PT_col.as<int32_t>() : nullptr,
+            tr ? tr->PT_val.as<double>() : nullptr, tr ? tr->PT_rowsum_inv.as<double>() : nullptr, o.restrict_mode,
+            C.W, C.g2, C.ldw);
+        cnt.launches += 1;
+        MG_CUDA(cudaGetLastError());
+        // Phi_c(u2_{c-1}) for all coarse points c = 1..Nc: one batched coarse step
+        PhiIO io;
+        io.k = (int)C.N;
+        io.xprev = C.W;
+        io.ld_prev = C.ldw;
+        io.guess = C.W + 1;
+        io.ld_guess = C.ldw;
+        io.xout = C.Vc;
+        io.ld_out = C.ldw;
+        io.signs = signs;
+        io.t0 = C.stride;
+        io.tstride = C.stride;
+        phi_batch(c, *C.op, io, o.solver, &cnt);
+        k_fas_rhs<<<nblk(C.n * (C.N + 1)), 256, 0, c->stream>>>(C.n, C.N, C.W, C.g2, C.Vc, C.ldw, C.gview(), C.view());
+        cnt.launches += 1;
+        MG_CUDA(cudaGetLastError());
+        cycle(l + 1);
+        k_correct<<<nblk(F.n * F.NT), 256, 0, c->stream>>>(F.n, F.NT, F.U, F.ld, C.view(), C.W, C.ldw,
+                                                          tr ? tr->P_ptr.as<int32_t>() : nullptr,
+                                                          tr ? tr->P_col.as<int32_t>() : nullptr,
+                                                          tr ? tr->P_val.as<double>() : nullptr);
+        cnt.launches += 1;
+        MG_CUDA(cudaGetLastError());
+    }
+
+    void cycle(int l) {
+        if (l == (int)lv.size() - 1) {
+            sequential_level(l);
+            return;
+        }
+        relax(l);
+        residual(l);
+        coarse_correction(l);
+        f_relax(l);
+    }
+
+    double read_norm() {
+        double h = 0.0;
+        MG_CUDA(cudaMemcpyAsync(&h, norm, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        MG_CUDA(cudaStreamSynchronize(c->stream));
+        return std::sqrt(h);
+    }
+};
+
+void check_solver_opts(const mg_solver_opts& so) {
+    if (so.max_cg < 1 || so.max_refine < 0 || !(so.cg_tol >= 0.0) || !(so.refine_tol >= 0.0) ||
+        !(so.inner_tol >= 0.0) || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) || so.cluster < 0 ||
+        so.cluster > 8 || !(so.tile == 0 || so.tile == 1 || so.tile == 8 || so.tile == 16 || so.tile == 32) ||
+        (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID) || so.smooth < 0 || so.smooth > 8 ||
+        !(so.omega >= 0.0 && so.omega < 2.0))
+        mg_fail(MG_EINVAL, "bad solver options");
+}
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+void reset_counters(mg_ctx* c) {
+    c->counters.ensure(16);
+    int64_t init[2] = {0, 0};
+    MG_CUDA(cudaMemcpyAsync(c->counters.p, init, 16, cudaMemcpyHostToDevice, c->stream));
+}
+
+void fill_stats(mg_ctx* c, const SolveCounters& cnt, mg_stats* st) {
+    unsigned char h[16];
+    MG_CUDA(cudaMemcpyAsync(h, c->counters.p, 16, cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+    unsigned long long it;
+    int worst;
+    std::memcpy(&it, h, 8);
+    std::memcpy(&worst, h + 8, 4);
+    st->cg_iters = (int64_t)it;
+    st->step_solves = cnt.step_solves;
+    st->batched_steps = cnt.batched_steps;
+    st->launches = cnt.launches;
+    if (worst < st->worst_status || st->worst_status == 0) st->worst_status = worst;
+}
+
+using clk = std::chrono::steady_clock;
+double secs(clk::time_point a, clk::time_point b) { return std::chrono::duration<double>(b - a).count(); }
+
+mg_status sequential_impl(mg_ctx* c, int level, int64_t N, double T, const double* a0, double* out,
+                          const mg_solver_opts* opts, mg_stats* stats) {
+    mg_solver_opts so;
+    if (opts) so = *opts;
+    else mg_solver_defaults(&so);
+    check_solver_opts(so);
+    if (level < 0 || level >= (int)c->meshes.size() || N <= 0 || !(T > 0.0) || !a0 || !out)
+        mg_fail(MG_EINVAL, "mg_sequential: bad arguments");
+    auto t0 = clk::now();
+    ctx_finalize(c);
+    const int64_t n = c->meshes[level].n;
+    StepOp& op = ctx_step_op(c, level, T / (double)N);
+    const int8_t* signs = ctx_pwm_table(c, N, T);
+    reset_counters(c);
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        MG_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    auto t1 = clk::now();
+    SolveCounters cnt;
+    MG_CUDA(cudaMemcpyAsync(out, a0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    for (int64_t t = 1; t <= N; ++t) {
+        PhiIO io;
+        io.k = 1;
+        io.xprev = out + (t - 1) * n;
+        io.ld_prev = 1;
+        io.guess = out + (t - 1) * n;  // previous step as the initial guess
+        io.ld_guess = 1;
+        io.xout = out + t * n;
+        io.ld_out = 1;
+        io.signs = signs;
+        io.t0 = t;
+        io.tstride = 0;
+        phi_batch(c, op, io, so, &cnt);
+    }
+    if (stats) {
+        fill_stats(c, cnt, stats);
+        auto t2 = clk::now();
+        stats->t_setup = secs(t0, t1);
+        stats->t_solve = secs(t1, t2);
+        if (stats->worst_status != 0) return (mg_status)stats->worst_status;
+    }
+    return MG_OK;
+}
+
+mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* out, const mg_opts* opts,
+                     mg_stats* stats) {
+    mg_opts o;
+    if (opts) o = *opts;
+    else mg_opts_defaults(&o);
+    check_solver_opts(o.solver);
+    if (N <= 0 || !(T > 0.0) || !a0 || !out || o.levels < 1 || o.levels > 8 || o.relax < 0 || o.relax > 4 ||
+        o.max_iter < 0 || !(o.tol >= 0.0) || o.restrict_mode < 0 || o.restrict_mode > 2)
+        mg_fail(MG_EINVAL, "mg_solve: bad arguments");
+    auto t0 = clk::now();
+    ctx_finalize(c);
+    for (int l = 0; l < o.levels; ++l)
+        if (o.space_level[l] < 0 || o.space_level[l] >= (int)c->meshes.size())
+            mg_fail(MG_EINVAL, "mg_solve: bad space level");
+    if (o.levels == 1) {
+        mg_solver_opts so = o.solver;
+        mg_status st = sequential_impl(c, o.space_level[0], N, T, a0, out, &so, stats);
+        if (stats) stats->iters = 0;
+        return st;
+    }
+    Solver S{c, N, T, o};
+    S.lv.resize(o.levels);
+    int64_t stride = 1;
+    for (int l = 0; l < o.levels; ++l) {
+        Level& L = S.lv[l];
+        L.mesh = o.space_level[l];
+        L.n = c->meshes[L.mesh].n;
+        if (N % stride) mg_fail(MG_EINVAL, "N must be divisible by the product of the coarsening factors");
+        L.N = N / stride;
+        L.stride = stride;
+        L.dt = T / (double)L.N;
+        L.op = &ctx_step_op(c, L.mesh, L.dt);
+        if (l < o.levels - 1) {
+            L.m = o.m[l];
+            if (L.m < 1 || L.N % L.m) mg_fail(MG_EINVAL, "N must be divisible by the product of the coarsening factors");
+            L.NT = L.N / L.m;
+            L.ld = round_up(L.NT + 1, 4);
+            int cm = o.space_level[l + 1];
+            if (cm != L.mesh) {
+                if (c->meshes[cm].n > L.n) mg_fail(MG_EINVAL, "coarse space level must not be finer");
+                L.tr = &ctx_transfer(c, L.mesh, cm);
+            }
+            stride *= L.m;
+        } else {
+            L.m = 0;
+            L.NT = L.N;
+            L.ld = 0;
+        }
+    }
+    // storage
+    size_t bytes = 0;
+    std::vector<size_t> sizes;
+    auto plan = [&](size_t nd) { sizes.push_back(nd * sizeof(double)); };
+    for (int l = 0; l < o.levels; ++l) {
+        Level& L = S.lv[l];
+        if (L.m) {
+            plan(L.m * L.n * L.ld);                 // U
+            plan(l ? L.m * L.n * L.ld : 0);         // G
+            plan(L.n * L.ld);                       // R
+            plan(L.n * L.ld);                       // V
+        } else {
+            plan((L.N + 1) * L.n);                  // U
+            plan((L.N + 1) * L.n);                  // G
+            plan(0);
+            plan(0);
+        }
+        if (l > 0) {
+            L.ldw = round_up(L.N + 1, 4);
+            plan(L.n * L.ldw);  // W
+            plan(L.n * L.ldw);  // g2
+            plan(L.n * L.ldw);  // Vc
+        } else {
+            plan(0);
+            plan(0);
+            plan(0);
+        }
+    }
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    for (auto s : sizes) bytes += r256(s);
+    bytes += r256(S.kRedBlocks * sizeof(double)) + r256(sizeof(double));
+    // one pooled allocation, carved per level
+    c->solve_buf[0].ensure(bytes);
+    char* p = (char*)c->solve_buf[0].p;
+    auto take = [&](size_t b) -> double* {
+        double* r = b ? (double*)p : nullptr;
+        p += (b + 255) / 256 * 256;
+        return r;
+    };
+    size_t q = 0;
+    for (int l = 0; l < o.levels; ++l) {
+        Level& L = S.lv[l];
+        L.U = take(sizes[q++]);
+        L.G = take(sizes[q++]);
+        L.R = take(sizes[q++]);
+        L.V = take(sizes[q++]);
+        L.W = take(sizes[q++]);
+        L.g2 = take(sizes[q++]);
+        L.Vc = take(sizes[q++]);
+    }
+    S.partial = take(S.kRedBlocks * sizeof(double));
+    S.norm = take(sizeof(double));
+    S.signs = ctx_pwm_table(c, N, T);
+    reset_counters(c);
+    Level& L0 = S.lv[0];
+    MG_CUDA(cudaMemsetAsync(L0.U, 0, L0.m * L0.n * L0.ld * sizeof(double), c->stream));
+    k_fill_column<<<nblk(L0.n), 256, 0, c->stream>>>(L0.n, a0, L0.U, L0.ld);
+    S.cnt.launches += 1;
+    MG_CUDA(cudaGetLastError());
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+    auto t1 = clk::now();
+    std::vector<double> hist;
+    double r0 = 0.0;
+    int it = 0;
+    bool converged = false;
+    for (it = 0;; ++it) {
+        S.relax(0);
+        S.residual(0);
+        double rn = S.read_norm();
+        hist.push_back(rn);
+        if (it == 0) r0 = rn;
+        double ref = o.tol_relative ? r0 : 1.0;
+        if (rn <= o.tol * ref) {
+            converged = true;
+            break;
+        }
+        if (!(rn == rn) || it >= o.max_iter) break;
+        S.coarse_correction(0);
+    }
+    k_to_time_major<<<nblk(L0.n * (N + 1)), 256, 0, c->stream>>>(L0.n, N, L0.view(), out);
+    S.cnt.launches += 1;
+    MG_CUDA(cudaGetLastError());
+    if (stats) {
+        fill_stats(c, S.cnt, stats);
+        auto t2 = clk::now();
+        stats->iters = it;
+        stats->n_hist = (int)std::min<size_t>(hist.size(), 64);
+        for (int k = 0; k < stats->n_hist; ++k) stats->res_hist[k] = hist[k];
+        stats->t_setup = secs(t0, t1);
+        stats->t_solve = secs(t1, t2);
+        if (stats->worst_status != 0) return (mg_status)stats->worst_status;
+    }
+    return converged ? MG_OK : MG_EMGRIT_MAXIT;
+}
+
+}  // namespace
+
+extern mg_status mg_guarded_call(mg_ctx* c, void (*fn)(void*), void* arg);
+
+template <class F>
+static mg_status run(mg_ctx* c, F&& f) {
+    mg_status out = MG_OK;
+    struct Box {
+        F* f;
+        mg_status* out;
+    } box{&f, &out};
+    mg_status st = mg_guarded_call(
+        c, [](void* a) { auto* b = (Box*)a; *b->out = (*b->f)(); }, &box);
+    return st != MG_OK ? st : out;
+}
+
+extern "C" {
+
+void mg_solver_defaults(mg_solver_opts* s) {
+    if (!s) return;
+    std::memset(s, 0, sizeof(*s));
+    s->cg_tol = 1e-13;
+    s->refine_tol = 1e-13;
+    s->inner_tol = 1e-5;
+    s->max_cg = 2000;
+    s->max_refine = 30;
+    s->precision = MG_FP64;
+    s->cluster = 0;
+    s->tile = 0;
+    s->precond = MG_PRECOND_MULTIGRID;
+    s->smooth = 2;
+    s->omega = 0.7;
+}
+
+void mg_opts_defaults(mg_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->levels = 2;
+    for (int l = 0; l < 8; ++l) o->m[l] = 16;
+    o->relax = 1;
+    o->tol = 1e-10;
+    o->tol_relative = 1;
+    o->max_iter = 50;
+    o->restrict_mode = 2;
+    mg_solver_defaults(&o->solver);
+}
+
+mg_status mg_step(mg_ctx* c, int level, int64_t N, double T, int64_t dt_mult, int k, int64_t i0, int64_t istride,
+                  const double* x_in, int64_t ld_in, double* x_out, int64_t ld_out, int guess,
+                  const mg_solver_opts* opts, mg_stats* stats) {
+    return run(c, [&]() -> mg_status {
+        mg_solver_opts so;
+        if (opts) so = *opts;
+        else mg_solver_defaults(&so);
+        check_solver_opts(so);
+        if (level < 0 || level >= (int)c->meshes.size() || N <= 0 || !(T > 0.0) || dt_mult <= 0 || k <= 0 ||
+            !x_in || !x_out || ld_in < k || ld_out < k || i0 < 0 || i0 > N || istride < 0 ||
+            i0 + (int64_t)(k - 1) * istride > N)
+            mg_fail(MG_EINVAL, "mg_step: bad arguments");
+        ctx_finalize(c);
+        StepOp& op = ctx_step_op(c, level, (double)dt_mult * T / (double)N);
+        const int8_t* signs = ctx_pwm_table(c, N, T);
+        reset_counters(c);
+        auto t1 = clk::now();
+        PhiIO io;
+        io.k = k;
+        io.xprev = x_in;
+        io.ld_prev = ld_in;
+        io.guess = guess ? x_out : nullptr;
+        io.ld_guess = ld_out;
+        io.xout = x_out;
+        io.ld_out = ld_out;
+        io.signs = signs;
+        io.t0 = i0;
+        io.tstride = istride;
+        SolveCounters cnt;
+        phi_batch(c, op, io, so, &cnt);
+        if (stats) {
+            std::memset(stats, 0, sizeof(*stats));
+            fill_stats(c, cnt, stats);
+            stats->t_solve = secs(t1, clk::now());
+            if (stats->worst_status != 0) return (mg_status)stats->worst_status;
+        }
+        return MG_OK;
+    });
+}
+
+mg_status mg_sequential(mg_ctx* c, int level, int64_t N, double T, const double* a0, double* out,
+                        const mg_solver_opts* opts, mg_stats* stats) {
+    return run(c, [&]() { return sequential_impl(c, level, N, T, a0, out, opts, stats); });
+}
+
+mg_status mg_solve(mg_ctx* c, int64_t N, double T, const double* a0, double* out, const mg_opts* opts,
+                   mg_stats* stats) {
+    return run(c, [&]() { return solve_impl(c, N, T, a0, out, opts, stats); });
+}
+
+mg_status mg_solve_host(mg_ctx* c, int64_t N, double T, const double* a0_host, double* out_host, const mg_opts* opts,
+                        mg_stats* stats) {
+    return run(c, [&]() -> mg_status {
+        if (!a0_host || !out_host || N <= 0) mg_fail(MG_EINVAL, "mg_solve_host: bad arguments");
+        mg_opts o;
+        if (opts) o = *opts;
+        else mg_opts_defaults(&o);
+        if (o.space_level[0] < 0 || o.space_level[0] >= (int)c->meshes.size())
+            mg_fail(MG_EINVAL, "mg_solve_host: bad space level");
+        const int64_t n = c->meshes[o.space_level[0]].n;
+        c->host_in.ensure(n * sizeof(double));
+        c->host_out.ensure((size_t)(N + 1) * n * sizeof(double));
+        MG_CUDA(cudaMemcpyAsync(c->host_in.p, a0_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        mg_status st = solve_impl(c, N, T, c->host_in.as<double>(), c->host_out.as<double>(), &o, stats);
+        MG_CUDA(cudaMemcpyAsync(out_host, c->host_out.p, (size_t)(N + 1) * n * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+        MG_CUDA(cudaStreamSynchronize(c->stream));
+        return st;
+    });
+}
+
+mg_status mg_sequential_host(mg_ctx* c, int level, int64_t N, double T, const double* a0_host, double* out_host,
+                             const mg_solver_opts* opts, mg_stats* stats) {
+    return run(c, [&]() -> mg_status {
+        if (!a0_host || !out_host || N <= 0 || level < 0 || level >= (int)c->meshes.size())
+            mg_fail(MG_EINVAL, "mg_sequential_host: bad arguments");
+        const int64_t n = c->meshes[level].n;
+        c->host_in.ensure(n * sizeof(double));
+        c->host_out.ensure((size_t)(N + 1) * n * sizeof(double));
+        MG_CUDA(cudaMemcpyAsync(c->host_in.p, a0_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        mg_status st = sequential_impl(c, level, N, T, c->host_in.as<double>(), c->host_out.as<double>(), opts, stats);
+        MG_CUDA(cudaMemcpyAsync(out_host, c->host_out.p, (size_t)(N + 1) * n * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+        MG_CUDA(cudaStreamSynchronize(c->stream));
+        return st;
+    });
+}
+
+}  // extern "C"
