@@ -132,7 +132,7 @@ typedef struct {
     int max_cg;         /* iteration limit of one (inner) PCG                              */
     int max_refine;     /* FP32+refinement: limit of outer sweeps                          */
     int precision;      /* mg_precision                                                    */
-    int cluster;        /* CTAs per cluster (1..8), 0 = library choice                     */
+    int cluster;        /* CTAs per cluster (1..16; above 8 needs non-portable clusters), 0 = default 8 */
     int tile;           /* columns per cluster (1, 8, 16, 32), 0 = library choice          */
     int precond;        /* mg_precond                                                      */
     int smooth;         /* damped-Jacobi sweeps before and after each coarse correction    */

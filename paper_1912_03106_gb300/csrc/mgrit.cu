@@ -307,7 +307,7 @@ struct Solver {
 void check_solver_opts(const mg_solver_opts& so) {
     if (so.max_cg < 1 || so.max_refine < 0 || !(so.cg_tol >= 0.0) || !(so.refine_tol >= 0.0) ||
         !(so.inner_tol >= 0.0) || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) || so.cluster < 0 ||
-        so.cluster > 8 || !(so.tile == 0 || so.tile == 1 || so.tile == 8 || so.tile == 16 || so.tile == 32) ||
+        so.cluster > 16 || !(so.tile == 0 || so.tile == 1 || so.tile == 8 || so.tile == 16 || so.tile == 32) ||
         (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID) || so.smooth < 0 || so.smooth > 8 ||
         !(so.omega >= 0.0 && so.omega < 2.0))
         mg_fail(MG_EINVAL, "bad solver options");

@@ -53,10 +53,22 @@ namespace {
 constexpr int NT = 256;  // threads per CTA
 constexpr int NWARP = NT / 32;
 constexpr int WMAX = 8;  // ELL entries handled fully unrolled; wider rows loop
-constexpr int RB = 2;    // rows whose loads are issued together
+#ifndef MG_RB
+#define MG_RB 2
+#endif
+#ifndef MG_MINB
+#define MG_MINB 1
+#endif
+// Work vectors are read through L1 (MG_L1 = 1) or from L2 only (0).  L1 reads are
+// coherent here because every phase that reads data written by other CTAs is
+// separated from the writes by a cluster barrier with acquire semantics.
+#ifndef MG_L1
+#define MG_L1 0
+#endif
+constexpr int RB = MG_RB;  // rows whose loads are issued together
 
 struct DepthArgs {
-    int64_t n;
+    int n;
     int W;
     const int32_t* col;  // W x n
     const double* L64;
@@ -129,7 +141,11 @@ __device__ __forceinline__ void vld(const T* p, T (&o)[V]) {
         o[2] = b.x;
         o[3] = b.y;
     } else {
+#if MG_L1
+        typename VT<T, V>::t v = *reinterpret_cast<const typename VT<T, V>::t*>(p);
+#else
         typename VT<T, V>::t v = __ldcg(reinterpret_cast<const typename VT<T, V>::t*>(p));
+#endif
         const T* e = reinterpret_cast<const T*>(&v);
 #pragma unroll
         for (int q = 0; q < V; ++q) o[q] = e[q];
@@ -146,7 +162,11 @@ __device__ __forceinline__ void vst(T* p, const T (&o)[V]) {
         T* e = reinterpret_cast<T*>(&v);
 #pragma unroll
         for (int q = 0; q < V; ++q) e[q] = o[q];
+#if MG_L1
+        *reinterpret_cast<typename VT<T, V>::t*>(p) = v;
+#else
         __stcg(reinterpret_cast<typename VT<T, V>::t*>(p), v);
+#endif
     }
 }
 
@@ -199,24 +219,25 @@ struct Lanes {
     static constexpr int TPR = KT / V;    // threads per row
     static constexpr int RPP = NT / TPR;  // rows per pass of the CTA
     static __device__ __forceinline__ int c0() { return (threadIdx.x % TPR) * V; }
-    static __device__ __forceinline__ int64_t roff() { return threadIdx.x / TPR; }
+    static __device__ __forceinline__ int roff() { return threadIdx.x / TPR; }
 };
 
 // Run a phase over the CTA's rows of an n-row level: loads of RB rows, then stores.
 template <int KT, int V, class B>
 __device__ __forceinline__ void run_rows(const Ctx<KT>& c, int64_t n, B& b) {
-    int64_t rb, re;
-    c.rows(n, rb, re);
+    int64_t rb64, re64;
+    c.rows(n, rb64, re64);
+    const int rb = (int)rb64, re = (int)re64;
     using Ln = Lanes<KT, V>;
-    for (int64_t base = rb + Ln::roff(); base < re; base += (int64_t)RB * Ln::RPP) {
+    for (int base = rb + Ln::roff(); base < re; base += RB * Ln::RPP) {
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
-            const int64_t i = base + (int64_t)q * Ln::RPP;
+            const int i = base + q * Ln::RPP;
             if (i < re) b.load(q, i);
         }
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
-            const int64_t i = base + (int64_t)q * Ln::RPP;
+            const int i = base + q * Ln::RPP;
             if (i < re) b.store(q, i);
         }
     }
@@ -224,8 +245,8 @@ __device__ __forceinline__ void run_rows(const Ctx<KT>& c, int64_t n, B& b) {
 
 // acc[e] = sum_w val[w, i] * v[col[w, i]][c0 + e]  (v tile-major with KT columns)
 template <int KT, int V, class A, class VAL, class X>
-__device__ __forceinline__ void ell_vec(const int32_t* __restrict__ col, const VAL* __restrict__ val, int64_t n,
-                                        int W, int64_t i, const X* v, int c0, A (&acc)[V]) {
+__device__ __forceinline__ void ell_vec(const int32_t* __restrict__ col, const VAL* __restrict__ val, int n, int W,
+                                        int i, const X* v, int c0, A (&acc)[V]) {
 #pragma unroll
     for (int e = 0; e < V; ++e) acc[e] = 0;
     int32_t j[WMAX];
@@ -233,21 +254,21 @@ __device__ __forceinline__ void ell_vec(const int32_t* __restrict__ col, const V
 #pragma unroll
     for (int w = 0; w < WMAX; ++w)
         if (w < W) {
-            j[w] = __ldg(col + (int64_t)w * n + i);
-            a[w] = __ldg(val + (int64_t)w * n + i);
+            j[w] = __ldg(col + w * n + i);
+            a[w] = __ldg(val + w * n + i);
         }
 #pragma unroll
     for (int w = 0; w < WMAX; ++w)
         if (w < W) {
             X xv[V];
-            vld<X, V>(v + (int64_t)j[w] * KT + c0, xv);
+            vld<X, V>(v + j[w] * KT + c0, xv);
 #pragma unroll
             for (int e = 0; e < V; ++e) acc[e] += (A)a[w] * (A)xv[e];
         }
     for (int w = WMAX; w < W; ++w) {
         X xv[V];
-        vld<X, V>(v + (int64_t)__ldg(col + (int64_t)w * n + i) * KT + c0, xv);
-        const A aw = (A)__ldg(val + (int64_t)w * n + i);
+        vld<X, V>(v + __ldg(col + w * n + i) * KT + c0, xv);
+        const A aw = (A)__ldg(val + w * n + i);
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[e] += aw * (A)xv[e];
     }
@@ -317,7 +338,7 @@ struct PhSmoothFirst {
     float w;
     int c0;
     float ri[RB][V], acc[RB][V], di[RB];
-    __device__ void load(int q, int64_t i) {
+    __device__ void load(int q, int i) {
         RT rv[V];
         vld<RT, V>(r + i * KT + c0, rv);
 #pragma unroll
@@ -325,7 +346,7 @@ struct PhSmoothFirst {
         ell_vec<KT, V, float>(D.col, D.LD32, D.n, D.W, i, r, c0, acc[q]);
         di[q] = __ldg(D.dinv32 + i);
     }
-    __device__ void store(int q, int64_t i) {
+    __device__ void store(int q, int i) {
         float xo[V], so[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
@@ -350,7 +371,7 @@ struct PhSmooth {
     bool last;
     double rz[V];
     float si[RB][V], xi[RB][V], acc[RB][V], di[RB], ri[RB][V];
-    __device__ void load(int q, int64_t i) {
+    __device__ void load(int q, int i) {
         vld<float, V>(src + i * KT + c0, si[q]);
         vld<float, V>(x + i * KT + c0, xi[q]);
         di[q] = __ldg(D.dinv32 + i);
@@ -362,7 +383,7 @@ struct PhSmooth {
             for (int e = 0; e < V; ++e) ri[q][e] = (float)rv[e];
         }
     }
-    __device__ void store(int q, int64_t i) {
+    __device__ void store(int q, int i) {
         float xo[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) xo[e] = xi[q][e] + w * di[q] * si[q][e];
@@ -386,10 +407,10 @@ struct PhRestrict {
     const DepthArgs& D;  // fine depth (holds P^T)
     const float* src;
     float* rc;
-    int64_t nc;
+    int nc;
     int c0;
     float acc[RB][V];
-    __device__ void load(int q, int64_t ic) {
+    __device__ void load(int q, int ic) {
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[q][e] = 0.0f;
         int32_t j[WMAX];
@@ -397,26 +418,26 @@ struct PhRestrict {
 #pragma unroll
         for (int w = 0; w < WMAX; ++w)
             if (w < D.rt_W) {
-                j[w] = __ldg(D.rt_col + (int64_t)w * nc + ic);
-                a[w] = __ldg(D.rt_w + (int64_t)w * nc + ic);
+                j[w] = __ldg(D.rt_col + w * nc + ic);
+                a[w] = __ldg(D.rt_w + w * nc + ic);
             }
 #pragma unroll
         for (int w = 0; w < WMAX; ++w)
             if (w < D.rt_W) {
                 float xv[V];
-                vld<float, V>(src + (int64_t)j[w] * KT + c0, xv);
+                vld<float, V>(src + j[w] * KT + c0, xv);
 #pragma unroll
                 for (int e = 0; e < V; ++e) acc[q][e] += a[w] * xv[e];
             }
         for (int w = WMAX; w < D.rt_W; ++w) {
             float xv[V];
-            vld<float, V>(src + (int64_t)__ldg(D.rt_col + (int64_t)w * nc + ic) * KT + c0, xv);
-            const float aw = __ldg(D.rt_w + (int64_t)w * nc + ic);
+            vld<float, V>(src + __ldg(D.rt_col + w * nc + ic) * KT + c0, xv);
+            const float aw = __ldg(D.rt_w + w * nc + ic);
 #pragma unroll
             for (int e = 0; e < V; ++e) acc[q][e] += aw * xv[e];
         }
     }
-    __device__ void store(int q, int64_t ic) { vst<float, V>(rc + ic * KT + c0, acc[q]); }
+    __device__ void store(int q, int ic) { vst<float, V>(rc + ic * KT + c0, acc[q]); }
 };
 
 // prolongation y = P x_c, x += y
@@ -427,7 +448,7 @@ struct PhProlong {
     float *x, *y;
     int c0;
     float yi[RB][V], xi[RB][V];
-    __device__ void load(int q, int64_t i) {
+    __device__ void load(int q, int i) {
 #pragma unroll
         for (int e = 0; e < V; ++e) yi[q][e] = 0.0f;
 #pragma unroll
@@ -436,14 +457,14 @@ struct PhProlong {
             if (p >= 0) {
                 const float wk = __ldg(D.pw + k * D.n + i);
                 float xv[V];
-                vld<float, V>(xc + (int64_t)p * KT + c0, xv);
+                vld<float, V>(xc + p * KT + c0, xv);
 #pragma unroll
                 for (int e = 0; e < V; ++e) yi[q][e] += wk * xv[e];
             }
         }
         vld<float, V>(x + i * KT + c0, xi[q]);
     }
-    __device__ void store(int q, int64_t i) {
+    __device__ void store(int q, int i) {
         float xo[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) xo[e] = xi[q][e] + yi[q][e];
@@ -460,11 +481,11 @@ struct PhResUpdate {
     float* s;
     int c0;
     float si[RB][V], acc[RB][V];
-    __device__ void load(int q, int64_t i) {
+    __device__ void load(int q, int i) {
         vld<float, V>(s + i * KT + c0, si[q]);
         ell_vec<KT, V, float>(D.col, D.L32, D.n, D.W, i, y, c0, acc[q]);
     }
-    __device__ void store(int q, int64_t i) {
+    __device__ void store(int q, int i) {
         float so[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) so[e] = si[q][e] - acc[q][e];
@@ -482,11 +503,11 @@ struct PhJacobi {
     double rz[V];
     RT ri[RB][V];
     float di[RB];
-    __device__ void load(int q, int64_t i) {
+    __device__ void load(int q, int i) {
         vld<RT, V>(r + i * KT + c0, ri[q]);
         di[q] = __ldg(D.dinv32 + i);
     }
-    __device__ void store(int q, int64_t i) {
+    __device__ void store(int q, int i) {
         float zo[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
@@ -655,13 +676,13 @@ struct PhPcgA {
     double pq[V];
     T lz[RB][V], pi[RB][V], qi[RB][V];
     float zi[RB][V];
-    __device__ void load(int k, int64_t i) {
+    __device__ void load(int k, int i) {
         ell_vec<KT, V, T>(D.col, Lv, D.n, D.W, i, z, c0, lz[k]);
         vld<float, V>(z + i * KT + c0, zi[k]);
         vld<T, V>(p + i * KT + c0, pi[k]);
         vld<T, V>(q + i * KT + c0, qi[k]);
     }
-    __device__ void store(int k, int64_t i) {
+    __device__ void store(int k, int i) {
         T po[V], qo[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
@@ -684,13 +705,13 @@ struct PhPcgB {
     int c0;
     double rr[V];
     T di[RB][V], ri[RB][V], pi[RB][V], qi[RB][V];
-    __device__ void load(int k, int64_t i) {
+    __device__ void load(int k, int i) {
         vld<T, V>(d + i * KT + c0, di[k]);
         vld<T, V>(r + i * KT + c0, ri[k]);
         vld<T, V>(p + i * KT + c0, pi[k]);
         vld<T, V>(q + i * KT + c0, qi[k]);
     }
-    __device__ void store(int k, int64_t i) {
+    __device__ void store(int k, int i) {
         T dn[V], rn[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
@@ -788,8 +809,8 @@ __device__ void pcg(Ctx<KT>& c, Smem<KT>& s, const PcgArgs& a, T* d, T* r, T* p,
 }
 
 // ---------------------------------------------------------------- the kernel
-template <int KT>
-__global__ void __launch_bounds__(NT, 1) k_phi_batch(PcgArgs a) {
+template <int KT, int MODE>
+__global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
     __shared__ Smem<KT> s;
     extern __shared__ float stage[];
     Ctx<KT> c;
@@ -861,7 +882,7 @@ __global__ void __launch_bounds__(NT, 1) k_phi_batch(PcgArgs a) {
         __syncthreads();
     }
 
-    if (a.mode == 0) {
+    if constexpr (MODE == 0) {
         if (threadIdx.x < KT) s.ref[threadIdx.x] = s.bb[threadIdx.x];
         __syncthreads();
         pcg<KT, double>(c, s, a, a.x64, a.r64, a.p64, a.q64, D.L64, a.tol * a.tol, stage);
@@ -941,10 +962,12 @@ __global__ void __launch_bounds__(NT, 1) k_phi_batch(PcgArgs a) {
     }
 }
 
-template <int KT>
-void launch(const PcgArgs& a, int csize, size_t stage_bytes, cudaStream_t stream) {
+template <int KT, int MODE>
+void launch_mode(const PcgArgs& a, int csize, size_t stage_bytes, cudaStream_t stream) {
     const int ntile = (a.k + KT - 1) / KT;
-    MG_CUDA(cudaFuncSetAttribute(k_phi_batch<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_bytes));
+    MG_CUDA(cudaFuncSetAttribute(k_phi_batch<KT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stage_bytes));
+    if (csize > 8) MG_CUDA(cudaFuncSetAttribute(k_phi_batch<KT, MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ntile * csize));
     cfg.blockDim = dim3(NT);
@@ -957,7 +980,13 @@ void launch(const PcgArgs& a, int csize, size_t stage_bytes, cudaStream_t stream
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    MG_CUDA(cudaLaunchKernelEx(&cfg, k_phi_batch<KT>, a));
+    MG_CUDA(cudaLaunchKernelEx(&cfg, k_phi_batch<KT, MODE>, a));
+}
+
+template <int KT>
+void launch(const PcgArgs& a, int csize, size_t stage_bytes, cudaStream_t stream) {
+    if (a.mode == 0) launch_mode<KT, 0>(a, csize, stage_bytes, stream);
+    else launch_mode<KT, 1>(a, csize, stage_bytes, stream);
 }
 
 }  // namespace
@@ -977,7 +1006,7 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
     const MeshLevel& m0 = c->meshes[op.mesh];
     const int KT = choose_tile(io.k, so.tile);
     int csize = so.cluster > 0 ? so.cluster : 8;
-    csize = std::max(1, std::min(8, csize));
+    csize = std::max(1, std::min(16, csize));
     const int ntile = (io.k + KT - 1) / KT;
     PcgArgs a = {};
     a.precond = so.precond;

@@ -10,7 +10,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmgrit_em.so")
+# MGRIT_EM_LIB may name another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("MGRIT_EM_LIB") or os.path.join(HERE, "libmgrit_em.so")
 
 MG_OK = 0
 STATUS = {
