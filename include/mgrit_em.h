@@ -169,6 +169,31 @@ mg_status mg_step(mg_ctx* ctx, int level, int64_t N, double T, int64_t dt_mult, 
                   double* x_out, int64_t ld_out, int guess, const mg_solver_opts* opts,
                   mg_stats* stats);
 
+/* mg_step without device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at the time of the
+ * call -- code being recorded into a CUDA graph by stream capture (where
+ * cudaMalloc is not allowed), callers running under an external memory manager
+ * or a fixed memory budget, and real-time loops that must not block in the
+ * allocator.  It computes exactly what mg_step computes (no FAS term g), but its
+ * work vectors live in one fixed-size array in device memory that the library
+ * declares statically: 32 MiB per device, held by every GPU that loads the
+ * library until the process exits.  Steps whose work vectors do not fit (about
+ * 60 bytes per unknown and column in the FP64 form, 3/4 of that with
+ * FP32+refinement, plus 1/3 more for the coarser multigrid levels) are rejected
+ * with MG_EINVAL and a message naming the bytes needed.
+ * It also allocates no operator: the step operator for (level, dt) and the PWM
+ * table for (N, T) must already exist, built by one regular mg_step call with the
+ * same arguments; otherwise MG_ESTATE.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (the kernel initialises everything it reads): calls whose kernels may
+ * overlap on the GPU -- other streams, other host threads -- race and must be
+ * serialised by the caller.  stats may be NULL (no synchronisation). */
+mg_status mg_step_static(mg_ctx* ctx, int level, int64_t N, double T, int64_t dt_mult, int k,
+                         int64_t i0, int64_t istride, const double* x_in, int64_t ld_in,
+                         double* x_out, int64_t ld_out, int guess, const mg_solver_opts* opts,
+                         mg_stats* stats);
+
 /* Sequential time stepping (forward block solve, Sec. 2): out[0] = a0,
  * out[i] = Phi_i(out[i-1]), i = 1..N, on mesh `level` with dt = T/N.
  * a0: n doubles; out: (N+1)*n doubles, time-major (device pointers). */

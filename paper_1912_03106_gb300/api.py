@@ -176,6 +176,19 @@ class Context:
         self._check(rc, allow=allow)
         return rc, stats_dict(st)
 
+    def mg_step_static(self, level, N, T, x_in, x_out, dt_mult=1, i0=1, istride=0, guess=False, solver=None,
+                       allow=()):
+        _dev64(x_in, "x_in")
+        _dev64(x_out, "x_out")
+        k = x_out.shape[1] if x_out.dim() == 2 else 1
+        ld_in = x_in.shape[1] if x_in.dim() == 2 else 1
+        st = L.mg_stats()
+        so = solver or solver_opts()
+        rc = self.lib.mg_step_static(self.h, level, N, T, dt_mult, k, i0, istride, _ptr(x_in), ld_in, _ptr(x_out),
+                                     k, int(bool(guess)), C.byref(so), C.byref(st))
+        self._check(rc, allow=allow)
+        return rc, stats_dict(st)
+
     def mg_sequential(self, level, N, T, a0, out, solver=None, allow=()):
         _dev64(a0, "a0")
         _dev64(out, "out")

@@ -157,6 +157,9 @@ void ctx_finalize(mg_ctx* c);
 StepOp& ctx_step_op(mg_ctx* c, int mesh, double dt);
 Transfer& ctx_transfer(mg_ctx* c, int fine, int coarse);
 const int8_t* ctx_pwm_table(mg_ctx* c, int64_t N, double T);
+// Lookups that never allocate: null if the operator / PWM table was not built yet.
+const StepOp* ctx_find_step_op(const mg_ctx* c, int mesh, double dt);
+const int8_t* ctx_find_pwm_table(const mg_ctx* c, int64_t N, double T);
 
 // ---- batched backward-Euler step (pcg.cu)
 struct PhiIO {

@@ -41,6 +41,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -1099,4 +1102,217 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
         counters->batched_steps += 1;
         counters->launches += 1;
     }
+}
+
+// ---------------------------------------------------------------- mg_step_static
+// A batched step whose work vectors live in one fixed, file-scope device array
+// instead of buffers the context allocates, for callers that must not allocate
+// device memory (see include/mgrit_em.h).  The array is per device and shared by
+// every call: calls whose kernels overlap on the GPU (other streams, other host
+// threads) race on it.
+#define MG_STATIC_SCRATCH_BYTES (32u << 20)
+
+static __device__ __align__(256) unsigned char g_step_scratch[MG_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+// Device address of g_step_scratch on the current device (looked up once per device).
+void* static_scratch(int device) {
+    if (device < 0 || device >= kMaxDevices) mg_fail(MG_EINVAL, "device id out of range for the static scratch");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_step_scratch);
+        if (e != cudaSuccess || !p)
+            mg_fail(MG_ECUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e));
+        g_scratch_addr[device] = p;
+    }
+    return g_scratch_addr[device];
+}
+
+}  // namespace
+
+extern mg_status mg_guarded_call(mg_ctx* c, void (*fn)(void*), void* arg);
+
+namespace {
+struct StaticStepCall {
+    mg_ctx* c;
+    int level;
+    int64_t N;
+    double T;
+    int64_t dt_mult;
+    int k;
+    int64_t i0, istride;
+    const double* x_in;
+    int64_t ld_in;
+    double* x_out;
+    int64_t ld_out;
+    int guess;
+    const mg_solver_opts* opts;
+    mg_stats* stats;
+    mg_status result;
+};
+
+void static_step(void* arg) {
+    StaticStepCall& q = *(StaticStepCall*)arg;
+    mg_ctx* c = q.c;
+    q.result = MG_OK;
+    mg_solver_opts so;
+    if (q.opts) so = *q.opts;
+    else mg_solver_defaults(&so);
+    if (q.level < 0 || q.level >= (int)c->meshes.size() || q.N <= 0 || !(q.T > 0.0) || q.dt_mult <= 0 || q.k <= 0 ||
+        !q.x_in || !q.x_out || q.ld_in < q.k || q.ld_out < q.k || q.i0 < 0 || q.i0 > q.N || q.istride < 0 ||
+        q.i0 + (int64_t)(q.k - 1) * q.istride > q.N)
+        mg_fail(MG_EINVAL, "mg_step_static: bad arguments");
+    if (so.max_cg < 1 || so.max_refine < 0 || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) ||
+        (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID) || so.cluster < 0 || so.cluster > 16 ||
+        !(so.tile == 0 || so.tile == 1 || so.tile == 8 || so.tile == 16 || so.tile == 32))
+        mg_fail(MG_EINVAL, "mg_step_static: bad solver options");
+    const double dt = (double)q.dt_mult * q.T / (double)q.N;
+    const StepOp* op = ctx_find_step_op(c, q.level, dt);
+    const int8_t* signs = ctx_find_pwm_table(c, q.N, q.T);
+    if (!op || !signs)
+        mg_fail(MG_ESTATE, "mg_step_static: the step operator or PWM table for this level, N, T and dt does not exist "
+                           "yet; one regular mg_step call with the same arguments builds both");
+    const MeshLevel& m0 = c->meshes[op->mesh];
+    const int KT = choose_tile(q.k, so.tile);
+    const int csize = std::max(1, std::min(16, so.cluster > 0 ? so.cluster : 8));
+    const int ntile = (q.k + KT - 1) / KT;
+    PcgArgs a = {};
+    a.precond = so.precond;
+    a.nu = so.smooth > 0 ? so.smooth : 2;
+    a.omega = so.omega > 0.0 ? (float)so.omega : 0.7f;
+    a.nd = a.precond == 1 ? (int)op->mg.size() : 1;
+    a.base_inv = (a.precond == 1 && op->base_inv.p) ? op->base_inv.as<float>() : nullptr;
+    // carve the work vectors out of the static array (256-byte aligned pieces)
+    const size_t e0 = (size_t)ntile * m0.n * KT;
+    std::vector<size_t> need;
+    if (so.precision == MG_FP64) need = {e0 * 8, e0 * 8, e0 * 8, e0 * 8};
+    else need = {e0 * 8, e0 * 8, e0 * 4, e0 * 4, e0 * 4, e0 * 4};
+    for (int d = 0; d < a.nd; ++d) {
+        const size_t ed = (size_t)ntile * op->mg[d]->n * KT * 4;
+        need.push_back(ed);
+        if (a.precond == 1 && d + 1 < a.nd) {
+            need.push_back(ed);
+            need.push_back(ed);
+            need.push_back(ed);
+        }
+        if (d > 0) need.push_back(ed);
+    }
+    size_t total = 256;  // counters
+    for (size_t b : need) total += (b + 255) / 256 * 256;
+    if (total > MG_STATIC_SCRATCH_BYTES)
+        mg_fail(MG_EINVAL, "mg_step_static: this step needs " + std::to_string(total) +
+                               " bytes of scratch; the static array holds " +
+                               std::to_string((size_t)MG_STATIC_SCRATCH_BYTES) + " (use fewer columns or mg_step)");
+    char* base = (char*)static_scratch(c->device);
+    char* p = base + 256;
+    size_t qi = 0;
+    auto take = [&]() -> void* {
+        void* r = p;
+        p += (need[qi++] + 255) / 256 * 256;
+        return r;
+    };
+    if (so.precision == MG_FP64) {
+        a.x64 = (double*)take();
+        a.r64 = (double*)take();
+        a.p64 = (double*)take();
+        a.q64 = (double*)take();
+    } else {
+        a.x64 = (double*)take();
+        a.b64 = (double*)take();
+        a.d32 = (float*)take();
+        a.r32 = (float*)take();
+        a.p32 = (float*)take();
+        a.q32 = (float*)take();
+    }
+    for (int d = 0; d < a.nd; ++d) {
+        const MgDepth& md = *op->mg[d];
+        const MeshLevel& mm = c->meshes[md.mesh];
+        DepthArgs& da = a.d[d];
+        da.n = (int)md.n;
+        da.W = md.W;
+        da.col = mm.ell_col.as<int32_t>();
+        da.L64 = md.L64.as<double>();
+        da.M64 = md.M64.as<double>();
+        da.L32 = md.L32.as<float>();
+        da.LD32 = md.LD32.as<float>();
+        da.dinv64 = md.dinv64.as<double>();
+        da.dinv32 = md.dinv32.as<float>();
+        if (d + 1 < a.nd) {
+            da.par = mm.par.as<int32_t>();
+            da.pw = mm.pw.as<float>();
+            da.rt_W = mm.rt_W;
+            da.rt_col = mm.rt_col.as<int32_t>();
+            da.rt_w = mm.rt_w.as<float>();
+        }
+        da.x = (float*)take();
+        if (a.precond == 1 && d + 1 < a.nd) {
+            da.sa = (float*)take();
+            da.sb = (float*)take();
+            da.y = (float*)take();
+        }
+        if (d > 0) da.r = (float*)take();
+    }
+    const size_t stage_bytes = a.base_inv ? (size_t)a.d[a.nd - 1].n * KT * sizeof(float) : 0;
+    if (stage_bytes > 200 * 1024) mg_fail(MG_EINVAL, "mg_step_static: base mesh too large for the dense coarse solve");
+    a.inv_dt = 1.0 / op->dt;
+    a.F = m0.F.as<double>();
+    a.J0 = c->pwm.J0;
+    a.signs = signs;
+    a.t0 = q.i0;
+    a.tstride = q.istride;
+    a.xprev = q.x_in;
+    a.ld_prev = q.ld_in;
+    a.g = nullptr;
+    a.ld_g = 0;
+    a.guess = q.guess ? q.x_out : nullptr;
+    a.ld_guess = q.ld_out;
+    a.xout = q.x_out;
+    a.ld_out = q.ld_out;
+    a.k = q.k;
+    a.tol = so.precision == MG_FP64 ? so.cg_tol : so.refine_tol;
+    a.inner_tol = so.inner_tol;
+    a.max_it = so.max_cg;
+    a.max_refine = so.max_refine;
+    a.mode = so.precision == MG_FP64 ? 0 : 1;
+    a.iter_sum = (unsigned long long*)base;
+    a.worst = (int*)(base + 8);
+    // the counters are the only scratch a step reads before writing it
+    MG_CUDA(cudaMemsetAsync(base, 0, 16, c->stream));
+    switch (KT) {
+        case 1: launch<1>(a, csize, stage_bytes, c->stream); break;
+        case 8: launch<8>(a, csize, stage_bytes, c->stream); break;
+        case 16: launch<16>(a, csize, stage_bytes, c->stream); break;
+        default: launch<32>(a, csize, stage_bytes, c->stream); break;
+    }
+    if (q.stats) {
+        unsigned char h[16];
+        MG_CUDA(cudaMemcpyAsync(h, base, 16, cudaMemcpyDeviceToHost, c->stream));
+        MG_CUDA(cudaStreamSynchronize(c->stream));
+        unsigned long long it;
+        int worst;
+        memcpy(&it, h, 8);
+        memcpy(&worst, h + 8, 4);
+        memset(q.stats, 0, sizeof(*q.stats));
+        q.stats->cg_iters = (int64_t)it;
+        q.stats->worst_status = worst;
+        q.stats->step_solves = q.k;
+        q.stats->batched_steps = 1;
+        q.stats->launches = 1;
+        if (worst != 0) q.result = (mg_status)worst;
+    }
+}
+}  // namespace
+
+extern "C" mg_status mg_step_static(mg_ctx* c, int level, int64_t N, double T, int64_t dt_mult, int k, int64_t i0,
+                                    int64_t istride, const double* x_in, int64_t ld_in, double* x_out,
+                                    int64_t ld_out, int guess, const mg_solver_opts* opts, mg_stats* stats) {
+    StaticStepCall q{c, level, N, T, dt_mult, k, i0, istride, x_in, ld_in, x_out, ld_out, guess, opts, stats, MG_OK};
+    mg_status st = mg_guarded_call(c, static_step, &q);
+    return st != MG_OK ? st : q.result;
 }

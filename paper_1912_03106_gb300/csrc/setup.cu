@@ -517,6 +517,17 @@ StepOp& ctx_step_op(mg_ctx* c, int mesh, double dt) {
     return *o;
 }
 
+const StepOp* ctx_find_step_op(const mg_ctx* c, int mesh, double dt) {
+    if (!c->finalized) return nullptr;
+    for (auto* o : c->ops)
+        if (o->mesh == mesh && o->dt == dt) return o;
+    return nullptr;
+}
+
+const int8_t* ctx_find_pwm_table(const mg_ctx* c, int64_t N, double T) {
+    return (c->pwm_N == N && c->pwm_T == T) ? c->pwm_table.as<int8_t>() : nullptr;
+}
+
 const int8_t* ctx_pwm_table(mg_ctx* c, int64_t N, double T) {
     if (!c->pwm.set) mg_fail(MG_ESTATE, "mg_set_pwm was not called");
     if (c->pwm_N == N && c->pwm_T == T) return c->pwm_table.as<int8_t>();

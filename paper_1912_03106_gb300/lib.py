@@ -97,6 +97,8 @@ _SIGNATURES = {
     "mg_opts_defaults": (None, [C.POINTER(mg_opts)]),
     "mg_step": (C.c_int, [_P, C.c_int, _I64, _D, _I64, C.c_int, _I64, _I64, _P, _I64, _P, _I64, C.c_int,
                           C.POINTER(mg_solver_opts), C.POINTER(mg_stats)]),
+    "mg_step_static": (C.c_int, [_P, C.c_int, _I64, _D, _I64, C.c_int, _I64, _I64, _P, _I64, _P, _I64, C.c_int,
+                                 C.POINTER(mg_solver_opts), C.POINTER(mg_stats)]),
     "mg_sequential": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P, C.POINTER(mg_solver_opts), C.POINTER(mg_stats)]),
     "mg_solve": (C.c_int, [_P, _I64, _D, _P, _P, C.POINTER(mg_opts), C.POINTER(mg_stats)]),
     "mg_solve_host": (C.c_int, [_P, _I64, _D, _P, _P, C.POINTER(mg_opts), C.POINTER(mg_stats)]),

@@ -1,0 +1,68 @@
+"""mg_step_static, the batched step that allocates nothing, against mg_step (GPU).
+
+Callers that cannot allocate device memory during a call (stream capture into a
+CUDA graph, external memory managers) use mg_step_static; its work vectors live
+in the library's fixed static device array.  Its results must equal those of the
+allocating mg_step within the step tolerance of the other step tests, on two
+calls in a row (the array keeps the previous call's contents).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import synth  # noqa: E402
+from synth.model import PwmSpec, machine_model  # noqa: E402
+from paper_1912_03106_gb300 import api  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def setup():
+    ctx = api.Context(0)
+    ids = api.setup_machine(ctx, synth.mesh_hierarchy(2), machine_model(pwm=PwmSpec(J0=1e6, f_carrier=5e3)))
+    yield ctx, ids
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_static_step_matches_allocating_step_twice(setup, precision):
+    ctx, ids = setup
+    level, N, T, k = ids[1], 256, 5e-3, 24
+    n = ctx.mg_num_dofs(level)
+    so = api.solver_opts(precision=precision, cg_tol=1e-14, refine_tol=1e-14)
+    rng = np.random.default_rng(11 + precision)
+    ref = torch.zeros((n, k), dtype=torch.float64, device="cuda")
+    x0 = torch.as_tensor(0.01 * rng.standard_normal((n, k)), device="cuda")
+    # one regular call builds the step operator and the PWM table
+    ctx.mg_step(level, N, T, x0, ref, dt_mult=2, i0=3, istride=5, solver=so)
+    for call in range(2):
+        x_in = torch.as_tensor(0.01 * rng.standard_normal((n, k)), device="cuda")
+        want = torch.zeros((n, k), dtype=torch.float64, device="cuda")
+        got = torch.full((n, k), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.mg_step(level, N, T, x_in, want, dt_mult=2, i0=3 + call, istride=5, solver=so)
+        _, st = ctx.mg_step_static(level, N, T, x_in, got, dt_mult=2, i0=3 + call, istride=5, solver=so)
+        w, g = want.cpu().numpy(), got.cpu().numpy()
+        err = np.linalg.norm(g - w, axis=0) / np.linalg.norm(w, axis=0)
+        assert err.max() <= 1e-11, (call, err.max())
+        assert st["worst_status"] == "MG_OK"
+
+
+def test_static_step_refuses_what_it_cannot_do(setup):
+    ctx, ids = setup
+    n = ctx.mg_num_dofs(ids[1])
+    x = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
+    # no operator for this dt yet: nothing is built on this path
+    with pytest.raises(api.L.MgError) as e:
+        ctx.mg_step_static(ids[1], 256, 5e-3, x, x.clone(), dt_mult=7)
+    assert e.value.status == -9
+    # beyond the static array
+    big = torch.zeros((n, 4096), dtype=torch.float64, device="cuda")
+    ctx.mg_step(ids[1], 4096, 5e-3, x, x.clone(), dt_mult=1, i0=1, istride=1)
+    with pytest.raises(api.L.MgError) as e:
+        ctx.mg_step_static(ids[1], 4096, 5e-3, big, big.clone(), dt_mult=1, i0=0, istride=1)
+    assert e.value.status == -1 and "static array" in str(e.value)
