@@ -122,6 +122,14 @@ typedef enum { MG_FP64 = 0, MG_FP32_REFINE = 1 } mg_precision;
 
 typedef enum { MG_PRECOND_JACOBI = 0, MG_PRECOND_MULTIGRID = 1 } mg_precond;
 
+/* How a batched step runs: MG_PATH_CLUSTER = one persistent launch, a thread-block
+ * cluster per tile of columns (lowest latency for few columns); MG_PATH_GRAPH =
+ * one kernel per phase over all columns, the iteration loop inside a CUDA graph
+ * (full-GPU throughput for many columns); MG_PATH_AUTO picks the graph path from
+ * MG_GRAPH_MIN_COLUMNS columns on.  Both compute the same step. */
+typedef enum { MG_PATH_AUTO = 0, MG_PATH_CLUSTER = 1, MG_PATH_GRAPH = 2 } mg_path;
+#define MG_GRAPH_MIN_COLUMNS 64
+
 typedef struct {
     /* linear solver of one backward-Euler step: batched PCG, preconditioned by
      * one FP32 geometric-multigrid V-cycle over the nested meshes (coarsest mesh
@@ -137,6 +145,7 @@ typedef struct {
     int precond;        /* mg_precond                                                      */
     int smooth;         /* damped-Jacobi sweeps before and after each coarse correction    */
     double omega;       /* Jacobi damping factor                                           */
+    int path;           /* mg_path                                                         */
 } mg_solver_opts;
 
 /* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,

@@ -1,0 +1,925 @@
+// Batched backward-Euler step solves for large batches: one high-occupancy kernel
+// per phase over all column tiles, the PCG loop inside one CUDA graph.
+//
+// Same mathematics as the cluster-resident kernel (pcg.cu): per column the step
+// of Eq. discrete_system solved by PCG with one FP32 multigrid V-cycle as the
+// preconditioner, FP64 form or FP32 inner iterations inside FP64 refinement.
+// Here every phase is its own kernel over a (tile, 256-row block) grid with
+// float4 / double2 lanes and a small register footprint, so all SMs run many
+// warps and the memory system, not latency, sets the pace.  Per-column dot
+// products are reduced in two deterministic stages: each block writes its
+// per-column partial, and a one-block scalar kernel adds the partials of all
+// row blocks in a fixed order and updates the per-column PCG scalars.  The
+// iteration loop is a graph conditional WHILE node whose condition the
+// convergence kernel sets on the device, so one graph launch runs a whole batched
+// step without host round trips.  The per-call arguments (pointers, time indices,
+// tolerances) are read from a small device struct, so the instantiated graph is
+// reused by every call with the same operator and tile count.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "vec.cuh"
+
+namespace {
+
+using namespace mgv;
+
+constexpr int G = 16;     // columns per tile
+constexpr int NTB = 256;  // threads per block
+constexpr int RBS = 256;  // rows per block
+
+struct CallArgs {
+    const double* xprev;
+    int64_t ld_prev;
+    const double* g;
+    int64_t ld_g;
+    const double* guess;
+    int64_t ld_guess;
+    double* xout;
+    int64_t ld_out;
+    const int8_t* signs;
+    int64_t t0, tstride;
+    int k;
+    double tol2;        // FP64 form: cg_tol^2; FP32+refine: refine_tol^2
+    double inner_tol2;  // FP32+refine inner reduction^2
+    int max_it;
+    int max_refine;
+};
+
+struct Depth {
+    int n, W, nrb;
+    const int32_t* col;
+    const double* L64;
+    const double* M64;
+    const float* L32;
+    const float* LD32;
+    const float* dinv32;
+    const int32_t* par;  // transfer to the next coarser depth
+    const float* pw;
+    int rt_W;
+    const int32_t* rt_col;
+    const float* rt_w;
+    float *x, *sa, *sb, *y, *r;
+};
+
+struct Cols {
+    double *bb, *gam, *beta, *alpha, *ref, *prev;
+    int *act, *outer, *iters;
+    int* ctr;  // [0] iterations of the current PCG, [1] refinement sweep
+};
+
+__device__ __forceinline__ void tile_rb(int nrb, int& t, int& rb) {
+    t = blockIdx.x / nrb;
+    rb = blockIdx.x - t * nrb;
+}
+
+// Per-block, per-column sum of the thread's V column partials into part[blockIdx.x * G + c].
+template <int V>
+__device__ __forceinline__ void block_partial(double (&v)[V], double* part) {
+    constexpr int TPR = G / V;
+    __shared__ double red[NTB / 32][G];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+#pragma unroll
+        for (int off = TPR; off < 32; off <<= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], off);
+    }
+    if (lane < TPR) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) red[warp][lane * V + e] = v[e];
+    }
+    __syncthreads();
+    if (threadIdx.x < G) {
+        double s = 0.0;
+        for (int w = 0; w < NTB / 32; ++w) s += red[w][threadIdx.x];
+        part[(size_t)blockIdx.x * G + threadIdx.x] = s;
+    }
+}
+
+// sum over the row blocks of column gc (fixed order)
+__device__ __forceinline__ double col_total(const double* part, int nrb, int gc) {
+    const int t = gc / G, l = gc % G;
+    double s = 0.0;
+    for (int rb = 0; rb < nrb; ++rb) s += part[((size_t)t * nrb + rb) * G + l];
+    return s;
+}
+
+template <class T>
+__device__ __forceinline__ T* tv(T* base, int n, int t) { return base + (size_t)t * n * G; }
+
+// ---------------------------------------------------------------- set-up and final phases
+// b = (1/dt) M x_prev + J0 sum_s b_s F_s, x0 = guess - g; FP64 form: r = b - L x0.
+template <int MODE>
+__global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restrict__ ca, double inv_dt,
+                                               const double* __restrict__ F, double J0, double* x64, double* r64,
+                                               double* p64, double* q64, double* b64, float* z, double* part_bb,
+                                               double* part_rr) {
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    const int lc = threadIdx.x % G, gc = t * G + lc;
+    const bool valid = gc < ca->k;
+    double sg[3] = {0.0, 0.0, 0.0};
+    if (valid) {
+        const int64_t tt = ca->t0 + (int64_t)gc * ca->tstride;
+        for (int q = 0; q < 3; ++q) sg[q] = (double)ca->signs[3 * tt + q];
+    }
+    const double* xprev = ca->xprev;
+    const double* guess = ca->guess;
+    const double* g = ca->g;
+    double bb[1] = {0.0}, rr[1] = {0.0};
+    const int i1 = min(D.n, (rb + 1) * RBS);
+    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+        double bi = 0.0, lx = 0.0, xi = 0.0;
+        if (valid) {
+            double mb = 0.0;
+            for (int w = 0; w < D.W; ++w) {
+                const int64_t j = __ldg(D.col + w * D.n + i);
+                mb += __ldg(D.M64 + w * D.n + i) * xprev[j * ca->ld_prev + gc];
+                if (guess) {
+                    double xj = guess[j * ca->ld_guess + gc];
+                    if (g) xj -= g[j * ca->ld_g + gc];
+                    lx += __ldg(D.L64 + w * D.n + i) * xj;
+                }
+            }
+            bi = mb * inv_dt + J0 * (sg[0] * F[i] + sg[1] * F[D.n + i] + sg[2] * F[2 * D.n + i]);
+            if (guess) {
+                xi = guess[(int64_t)i * ca->ld_guess + gc];
+                if (g) xi -= g[(int64_t)i * ca->ld_g + gc];
+            }
+        }
+        const size_t o = ((size_t)t * D.n + i) * G + lc;
+        x64[o] = xi;
+        z[o] = 0.0f;
+        if (MODE == 0) {
+            const double ri = bi - lx;
+            r64[o] = ri;
+            p64[o] = 0.0;
+            q64[o] = 0.0;
+            rr[0] += ri * ri;
+        } else {
+            b64[o] = bi;
+        }
+        bb[0] += bi * bi;
+    }
+    block_partial<1>(bb, part_bb);
+    if (MODE == 0) {
+        __syncthreads();
+        block_partial<1>(rr, part_rr);
+    }
+}
+
+// x_out = x + g
+__global__ void __launch_bounds__(NTB) kb_final(Depth D, const CallArgs* __restrict__ ca, const double* x64) {
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    const int lc = threadIdx.x % G, gc = t * G + lc;
+    if (gc >= ca->k) return;
+    const int i1 = min(D.n, (rb + 1) * RBS);
+    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+        double xi = x64[((size_t)t * D.n + i) * G + lc];
+        if (ca->g) xi += ca->g[(int64_t)i * ca->ld_g + gc];
+        ca->xout[(int64_t)i * ca->ld_out + gc] = xi;
+    }
+}
+
+// ---------------------------------------------------------------- scalar (one-block) phases
+constexpr int NSB = 1024;
+
+// FP64 form: ||b||^2, ||r0||^2 -> active columns, loop condition.
+__global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* part_bb, const double* part_rr, int nrb,
+                                                      int kpad, const CallArgs* __restrict__ ca,
+                                                      cudaGraphConditionalHandle h) {
+    int any = 0;
+    for (int c = threadIdx.x; c < kpad; c += NSB) {
+        const double bb = col_total(part_bb, nrb, c), rr = col_total(part_rr, nrb, c);
+        st.bb[c] = bb;
+        st.ref[c] = bb;
+        st.gam[c] = 0.0;
+        st.iters[c] = 0;
+        const int a = (c < ca->k) && !(rr <= ca->tol2 * bb);
+        st.act[c] = a;
+        any |= a;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        st.ctr[0] = 0;
+        cudaGraphSetConditional(h, (any && ca->max_it > 0) ? 1u : 0u);
+    }
+}
+
+// FP32+refinement: ||b||^2, every column starts in the refinement loop.
+__global__ void __launch_bounds__(NSB) kb_scalar_init1(Cols st, const double* part_bb, int nrb, int kpad,
+                                                      const CallArgs* __restrict__ ca, cudaGraphConditionalHandle h) {
+    for (int c = threadIdx.x; c < kpad; c += NSB) {
+        st.bb[c] = col_total(part_bb, nrb, c);
+        st.outer[c] = c < ca->k;
+        st.iters[c] = 0;
+        st.act[c] = 0;
+    }
+    if (threadIdx.x == 0) {
+        st.ctr[1] = 0;
+        cudaGraphSetConditional(h, 1u);
+    }
+}
+
+// (r, z) -> gamma, beta
+__global__ void __launch_bounds__(NSB) kb_scalar_gamma(Cols st, const double* part, int nrb, int kpad) {
+    const int first = st.ctr[0] == 0;
+    for (int c = threadIdx.x; c < kpad; c += NSB) {
+        const double gn = col_total(part, nrb, c);
+        st.beta[c] = (first || st.gam[c] == 0.0) ? 0.0 : gn / st.gam[c];
+        st.gam[c] = gn;
+    }
+}
+
+// (p, q) -> alpha
+__global__ void __launch_bounds__(NSB) kb_scalar_alpha(Cols st, const double* part, int nrb, int kpad) {
+    for (int c = threadIdx.x; c < kpad; c += NSB) {
+        const double pq = col_total(part, nrb, c);
+        st.alpha[c] = (st.act[c] && pq != 0.0) ? st.gam[c] / pq : 0.0;
+    }
+}
+
+// (r, r) -> convergence masks and the loop condition
+__global__ void __launch_bounds__(NSB) kb_scalar_conv(Cols st, const double* part, int nrb, int kpad,
+                                                     const CallArgs* __restrict__ ca, int inner,
+                                                     cudaGraphConditionalHandle h) {
+    const double tol2 = inner ? ca->inner_tol2 : ca->tol2;
+    int any = 0;
+    for (int c = threadIdx.x; c < kpad; c += NSB) {
+        if (st.act[c]) {
+            const double rr = col_total(part, nrb, c);
+            st.iters[c] += 1;
+            if (rr <= tol2 * st.ref[c] || !(rr == rr)) st.act[c] = 0;
+        }
+        any |= st.act[c];
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        const int it = st.ctr[0] + 1;
+        st.ctr[0] = it;
+        cudaGraphSetConditional(h, (any && it < ca->max_it) ? 1u : 0u);
+    }
+}
+
+// refinement decisions after r = b - L64 x; sets the inner and outer loop conditions
+__global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* part, int nrb, int kpad,
+                                                       const CallArgs* __restrict__ ca,
+                                                       cudaGraphConditionalHandle h_inner,
+                                                       cudaGraphConditionalHandle h_outer) {
+    const int sweep = st.ctr[1];
+    int any = 0;
+    for (int c = threadIdx.x; c < kpad; c += NSB) {
+        const double rr = col_total(part, nrb, c);
+        if (st.outer[c] == 1) {
+            const bool met = rr <= ca->tol2 * st.bb[c];
+            const bool stalled = sweep > 0 && rr > 0.25 * st.prev[c];
+            if (met || (stalled && rr <= 1e-16 * st.bb[c])) st.outer[c] = 0;
+            else if (stalled || sweep >= ca->max_refine || !(rr == rr)) st.outer[c] = 2;
+        }
+        const int a = st.outer[c] == 1;
+        st.act[c] = a;
+        st.ref[c] = rr;
+        st.prev[c] = rr;
+        st.gam[c] = 0.0;
+        any |= a;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        st.ctr[0] = 0;
+        st.ctr[1] = sweep + 1;
+        cudaGraphSetConditional(h_inner, (any && ca->max_it > 0) ? 1u : 0u);
+        cudaGraphSetConditional(h_outer, any ? 1u : 0u);
+    }
+}
+
+// statuses and iteration totals into the context counters
+__global__ void __launch_bounds__(NSB) kb_scalar_final(Cols st, int kpad, const CallArgs* __restrict__ ca, int mode,
+                                                      unsigned long long* iter_sum, int* worst) {
+    for (int c = threadIdx.x; c < kpad && c < ca->k; c += NSB) {
+        const int failed = mode == 0 ? st.act[c] : st.outer[c] != 0;
+        if (failed) atomicMin(worst, (int)MG_ECG_MAXIT);
+        atomicAdd(iter_sum, (unsigned long long)st.iters[c]);
+    }
+}
+
+// ---------------------------------------------------------------- multigrid phases (FP32, float4 lanes)
+constexpr int VF = 4;
+constexpr int TPRF = G / VF;       // threads per row
+constexpr int RPPF = NTB / TPRF;   // rows per pass
+
+#define ROWS_F(D, t, rb, i)                                   \
+    int t, rb;                                                \
+    tile_rb((D).nrb, t, rb);                                  \
+    const int c0 = (threadIdx.x % TPRF) * VF;                 \
+    const int _i1 = min((D).n, (rb + 1) * RBS);               \
+    for (int i = rb * RBS + threadIdx.x / TPRF; i < _i1; i += RPPF)
+
+// x = w D^-1 r, s = r - w (L D^-1) r
+template <class RT>
+__global__ void __launch_bounds__(NTB) kb_smooth_first(Depth D, const RT* rin_base, float w) {
+    ROWS_F(D, t, rb, i) {
+        const RT* rin = tv(rin_base, D.n, t);
+        RT rv[VF];
+        vld<RT, VF>(rin + i * G + c0, rv);
+        float acc[VF];
+        ell_vec<G, VF, float>(D.col, D.LD32, D.n, D.W, i, rin, c0, acc);
+        const float di = __ldg(D.dinv32 + i);
+        float xo[VF], so[VF];
+#pragma unroll
+        for (int e = 0; e < VF; ++e) {
+            xo[e] = w * di * (float)rv[e];
+            so[e] = (float)rv[e] - w * acc[e];
+        }
+        vst<float, VF>(tv(D.x, D.n, t) + i * G + c0, xo);
+        vst<float, VF>(tv(D.sa, D.n, t) + i * G + c0, so);
+    }
+}
+
+// x += w D^-1 s; s' = s - w (L D^-1) s if dst is given (not on a level's last sweep);
+// partial (r, x) if rtop is given (last sweep on the finest level)
+template <class RT>
+__global__ void __launch_bounds__(NTB) kb_smooth(Depth D, const float* src_base, float* dst_base, const RT* rtop_base,
+                                                 float w, double* part) {
+    double rz[VF] = {0.0, 0.0, 0.0, 0.0};
+    {
+        ROWS_F(D, t, rb, i) {
+            const float* src = tv(src_base, D.n, t);
+            float* x = tv(D.x, D.n, t);
+            float sv[VF], xv[VF];
+            vld<float, VF>(src + i * G + c0, sv);
+            vld<float, VF>(x + i * G + c0, xv);
+            const float di = __ldg(D.dinv32 + i);
+            float xo[VF];
+#pragma unroll
+            for (int e = 0; e < VF; ++e) xo[e] = xv[e] + w * di * sv[e];
+            vst<float, VF>(x + i * G + c0, xo);
+            if (rtop_base) {
+                RT rv[VF];
+                vld<RT, VF>(tv(rtop_base, D.n, t) + i * G + c0, rv);
+#pragma unroll
+                for (int e = 0; e < VF; ++e) rz[e] += (double)rv[e] * (double)xo[e];
+            }
+            if (dst_base) {  // the next residual is needed unless this is the last sweep
+                float acc[VF];
+                ell_vec<G, VF, float>(D.col, D.LD32, D.n, D.W, i, src, c0, acc);
+                float so[VF];
+#pragma unroll
+                for (int e = 0; e < VF; ++e) so[e] = sv[e] - w * acc[e];
+                vst<float, VF>(tv(dst_base, D.n, t) + i * G + c0, so);
+            }
+        }
+    }
+    if (rtop_base) block_partial<VF>(rz, part);
+}
+
+// r_c = P^T s over the coarse rows (grid over the coarse depth's row blocks)
+__global__ void __launch_bounds__(NTB) kb_restrict(Depth D, Depth C, const float* src_base) {
+    ROWS_F(C, t, rb, ic) {
+        const float* src = tv(src_base, D.n, t);
+        float acc[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int w = 0; w < D.rt_W; ++w) {
+            const int j = __ldg(D.rt_col + w * C.n + ic);
+            const float a = __ldg(D.rt_w + w * C.n + ic);
+            float xv[VF];
+            vld<float, VF>(src + j * G + c0, xv);
+#pragma unroll
+            for (int e = 0; e < VF; ++e) acc[e] += a * xv[e];
+        }
+        vst<float, VF>(tv(C.r, C.n, t) + ic * G + c0, acc);
+    }
+}
+
+// y = P x_c, x += y
+__global__ void __launch_bounds__(NTB) kb_prolong(Depth D, Depth C) {
+    ROWS_F(D, t, rb, i) {
+        const float* xc = tv(C.x, C.n, t);
+        float yv[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int p = __ldg(D.par + q * D.n + i);
+            if (p >= 0) {
+                const float wq = __ldg(D.pw + q * D.n + i);
+                float xv[VF];
+                vld<float, VF>(xc + p * G + c0, xv);
+#pragma unroll
+                for (int e = 0; e < VF; ++e) yv[e] += wq * xv[e];
+            }
+        }
+        float* x = tv(D.x, D.n, t);
+        float xv[VF];
+        vld<float, VF>(x + i * G + c0, xv);
+#pragma unroll
+        for (int e = 0; e < VF; ++e) xv[e] += yv[e];
+        vst<float, VF>(x + i * G + c0, xv);
+        vst<float, VF>(tv(D.y, D.n, t) + i * G + c0, yv);
+    }
+}
+
+// s -= L y
+__global__ void __launch_bounds__(NTB) kb_resupdate(Depth D, float* s_base) {
+    ROWS_F(D, t, rb, i) {
+        float* s = tv(s_base, D.n, t);
+        float acc[VF], sv[VF];
+        ell_vec<G, VF, float>(D.col, D.L32, D.n, D.W, i, tv(D.y, D.n, t), c0, acc);
+        vld<float, VF>(s + i * G + c0, sv);
+#pragma unroll
+        for (int e = 0; e < VF; ++e) sv[e] -= acc[e];
+        vst<float, VF>(s + i * G + c0, sv);
+    }
+}
+
+// coarsest level: x = A^-1 r (dense, FP32), 64 rows x one tile per block
+template <class RT>
+__global__ void __launch_bounds__(NTB) kb_base_dense(int n0, const float* __restrict__ A, const RT* r_base,
+                                                     float* x_base, int nrb64) {
+    __shared__ float As[64][33];
+    __shared__ float Rs[32][G];
+    const int t = blockIdx.x / nrb64, ib = blockIdx.x % nrb64;
+    const RT* r = r_base + (size_t)t * n0 * G;
+    const int row = threadIdx.x / 4, cg = (threadIdx.x % 4) * 4;
+    const int i = ib * 64 + row;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int j0 = 0; j0 < n0; j0 += 32) {
+        for (int q = threadIdx.x; q < 64 * 32; q += NTB) {
+            const int rr = q / 32, cc = q % 32;
+            const int gi = ib * 64 + rr, gj = j0 + cc;
+            As[rr][cc] = (gi < n0 && gj < n0) ? __ldg(A + (size_t)gi * n0 + gj) : 0.0f;
+        }
+        for (int q = threadIdx.x; q < 32 * G; q += NTB) {
+            const int jj = q / G, cc = q % G;
+            const int gj = j0 + jj;
+            Rs[jj][cc] = gj < n0 ? (float)r[(size_t)gj * G + cc] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int jj = 0; jj < 32; ++jj) {
+            const float a = As[row][jj];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[e] += a * Rs[jj][cg + e];
+        }
+        __syncthreads();
+    }
+    if (i < n0) vst<float, 4>(x_base + ((size_t)t * n0 + i) * G + cg, acc);
+}
+
+// coarsest level without a dense inverse, or Jacobi preconditioning: x = w D^-1 r
+template <class RT>
+__global__ void __launch_bounds__(NTB) kb_jacobi(Depth D, const RT* r_base, float w, double* part) {
+    double rz[VF] = {0.0, 0.0, 0.0, 0.0};
+    {
+        ROWS_F(D, t, rb, i) {
+            RT rv[VF];
+            vld<RT, VF>(tv(r_base, D.n, t) + i * G + c0, rv);
+            const float di = __ldg(D.dinv32 + i);
+            float xo[VF];
+#pragma unroll
+            for (int e = 0; e < VF; ++e) {
+                xo[e] = w * di * (float)rv[e];
+                rz[e] += (double)rv[e] * (double)xo[e];
+            }
+            vst<float, VF>(tv(D.x, D.n, t) + i * G + c0, xo);
+        }
+    }
+    if (part) block_partial<VF>(rz, part);
+}
+
+// ---------------------------------------------------------------- PCG update phases
+template <class T>
+struct VecOf {
+    static constexpr int V = std::is_same<T, double>::value ? 2 : 4;
+};
+
+// p = z + beta p, q = L z + beta q, partial (p, q)
+template <class T>
+__global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base, T* q_base, const double* beta,
+                                                double* part) {
+    constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    const int c0 = (threadIdx.x % TPR) * V;
+    double pq[V] = {};
+    T bt[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) bt[e] = (T)beta[t * G + c0 + e];
+    const float* z = tv((const float*)D.x, D.n, t);
+    T* p = tv(p_base, D.n, t);
+    T* q = tv(q_base, D.n, t);
+    const int i1 = min(D.n, (rb + 1) * RBS);
+    for (int i = rb * RBS + threadIdx.x / TPR; i < i1; i += RPP) {
+        T lz[V], pv[V], qv[V];
+        float zv[V];
+        ell_vec<G, V, T>(D.col, Lv, D.n, D.W, i, z, c0, lz);
+        vld<float, V>(z + i * G + c0, zv);
+        vld<T, V>(p + i * G + c0, pv);
+        vld<T, V>(q + i * G + c0, qv);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            pv[e] = (T)zv[e] + bt[e] * pv[e];
+            qv[e] = lz[e] + bt[e] * qv[e];
+            pq[e] += (double)pv[e] * (double)qv[e];
+        }
+        vst<T, V>(p + i * G + c0, pv);
+        vst<T, V>(q + i * G + c0, qv);
+    }
+    block_partial<V>(pq, part);
+}
+
+// d += alpha p, r -= alpha q, partial (r, r)
+template <class T>
+__global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, const T* p_base, const T* q_base,
+                                                const double* alpha, double* part) {
+    constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    const int c0 = (threadIdx.x % TPR) * V;
+    double rr[V] = {};
+    T al[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) al[e] = (T)alpha[t * G + c0 + e];
+    T* d = tv(d_base, D.n, t);
+    T* r = tv(r_base, D.n, t);
+    const T* p = tv(p_base, D.n, t);
+    const T* q = tv(q_base, D.n, t);
+    const int i1 = min(D.n, (rb + 1) * RBS);
+    for (int i = rb * RBS + threadIdx.x / TPR; i < i1; i += RPP) {
+        T dv[V], rv[V], pv[V], qv[V];
+        vld<T, V>(d + i * G + c0, dv);
+        vld<T, V>(r + i * G + c0, rv);
+        vld<T, V>(p + i * G + c0, pv);
+        vld<T, V>(q + i * G + c0, qv);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            dv[e] += al[e] * pv[e];
+            rv[e] -= al[e] * qv[e];
+            rr[e] += (double)rv[e] * (double)rv[e];
+        }
+        vst<T, V>(d + i * G + c0, dv);
+        vst<T, V>(r + i * G + c0, rv);
+    }
+    block_partial<V>(rr, part);
+}
+
+// FP32+refinement: r = b - L64 x for columns still refining (else 0); r32 = r, d = p = q = 0
+__global__ void __launch_bounds__(NTB) kb_refine_r(Depth D, const double* b64, const double* x64, float* r32,
+                                                   float* d32, float* p32, float* q32, const int* outer,
+                                                   double* part) {
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    const int lc = threadIdx.x % G, gc = t * G + lc;
+    const bool on = outer[gc] == 1;
+    double rr[1] = {0.0};
+    const double* x = tv(x64, D.n, t);
+    const int i1 = min(D.n, (rb + 1) * RBS);
+    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+        double ri = 0.0;
+        if (on) {
+            double lx[1];
+            ell_vec<G, 1, double>(D.col, D.L64, D.n, D.W, i, x, lc, lx);
+            ri = b64[((size_t)t * D.n + i) * G + lc] - lx[0];
+        }
+        const size_t o = ((size_t)t * D.n + i) * G + lc;
+        r32[o] = (float)ri;
+        d32[o] = 0.0f;
+        p32[o] = 0.0f;
+        q32[o] = 0.0f;
+        rr[0] += ri * ri;
+    }
+    block_partial<1>(rr, part);
+}
+
+__global__ void __launch_bounds__(NTB) kb_update_x(Depth D, double* x64, const float* d32, const int* outer) {
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    const int lc = threadIdx.x % G, gc = t * G + lc;
+    if (outer[gc] != 1) return;
+    const int i1 = min(D.n, (rb + 1) * RBS);
+    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+        const size_t o = ((size_t)t * D.n + i) * G + lc;
+        x64[o] += (double)d32[o];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- plan: buffers + graph
+struct GraphPlan {
+    const StepOp* op = nullptr;
+    int ntile = 0, precision = 0, precond = 1, nu = 2;
+    float omega = 0.7f;
+    std::vector<DBuf> bufs;
+    DBuf args, cols, part;
+    std::vector<Depth> depth;
+    Cols st{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr, cap3 = nullptr;
+    double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *b64 = nullptr;
+    float *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    ~GraphPlan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        if (cap2) cudaStreamDestroy(cap2);
+        if (cap3) cudaStreamDestroy(cap3);
+    }
+};
+
+void graph_plan_delete(GraphPlan* p) { delete p; }
+
+namespace {
+
+void* alloc(GraphPlan& P, size_t bytes) {
+    P.bufs.emplace_back();
+    P.bufs.back().ensure(bytes);
+    return P.bufs.back().p;
+}
+
+inline unsigned grid(int ntile, int nrb) { return (unsigned)(ntile * nrb); }
+
+// one preconditioner application on the capture stream: z = B r into depth[0].x;
+// the last kernel writes the (r, z) partials into part
+template <class RT>
+void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* part) {
+    const int nd = (int)P.depth.size();
+    const float w = P.omega;
+    if (P.precond == 0) {
+        Depth& D = P.depth[0];
+        kb_jacobi<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, rtop, 1.0f, part);
+        return;
+    }
+    std::vector<int> sel(nd, 0);
+    for (int d = 0; d < nd - 1; ++d) {
+        Depth& D = P.depth[d];
+        if (d == 0) kb_smooth_first<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, rtop, w);
+        else kb_smooth_first<float><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, D.r, w);
+        int sl = 0;
+        for (int sw = 1; sw < P.nu; ++sw) {
+            kb_smooth<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr, w,
+                                                              nullptr);
+            sl ^= 1;
+        }
+        sel[d] = sl;
+        Depth& C = P.depth[d + 1];
+        kb_restrict<<<grid(P.ntile, C.nrb), NTB, 0, s>>>(D, C, sl ? D.sb : D.sa);
+    }
+    Depth& B = P.depth[nd - 1];
+    const int nrb64 = (B.n + 63) / 64;
+    if (P.op->base_inv.p) {
+        if (nd == 1) kb_base_dense<RT><<<P.ntile * nrb64, NTB, 0, s>>>(B.n, P.op->base_inv.as<float>(), rtop, B.x, nrb64);
+        else kb_base_dense<float><<<P.ntile * nrb64, NTB, 0, s>>>(B.n, P.op->base_inv.as<float>(), B.r, B.x, nrb64);
+    } else {
+        if (nd == 1) kb_jacobi<RT><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, rtop, w, nullptr);
+        else kb_jacobi<float><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, B.r, w, nullptr);
+    }
+    if (nd == 1) {
+        // (r, z) for a single-level hierarchy: a no-op smoothing pass computes it
+        Depth& D = P.depth[0];
+        Depth Z = D;
+        Z.x = D.x;
+        // z is final; accumulate (r, z) with a zero-weight sweep
+        kb_smooth<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(Z, D.x, nullptr, rtop, 0.0f, part);
+        return;
+    }
+    for (int d = nd - 2; d >= 0; --d) {
+        Depth& D = P.depth[d];
+        Depth& C = P.depth[d + 1];
+        kb_prolong<<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, C);
+        int sl = sel[d];
+        kb_resupdate<<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa);
+        for (int sw = 0; sw < P.nu; ++sw) {
+            const bool last = sw == P.nu - 1;
+            const bool top = last && d == 0;
+            kb_smooth<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa, last ? nullptr : (sl ? D.sa : D.sb),
+                                                              top ? rtop : nullptr, w, top ? part : nullptr);
+            sl ^= 1;
+        }
+    }
+}
+
+// one PCG iteration body (after the preconditioner)
+template <class T>
+void capture_pcg_body(GraphPlan& P, cudaStream_t s, T* d, T* r, T* p, T* q, const T* Lv, const CallArgs* ca,
+                      int inner, cudaGraphConditionalHandle h) {
+    Depth& D0 = P.depth[0];
+    double* part = P.part.as<double>();
+    const int kpad = P.ntile * G;
+    capture_precondition<T>(P, s, r, part);
+    kb_scalar_gamma<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad);
+    kb_pcg_a<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
+    kb_scalar_alpha<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad);
+    kb_pcg_b<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, d, r, p, q, P.st.alpha, part);
+    kb_scalar_conv<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad, ca, inner, h);
+}
+
+// append a WHILE node at the capture's current position; returns its body graph
+cudaGraph_t add_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    MG_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    MG_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+    MG_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return prm.conditional.phGraph_out[0];
+}
+
+cudaGraphConditionalHandle new_handle(cudaStream_t s) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    MG_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle h;
+    MG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    return h;
+}
+
+GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so) {
+    auto* P = new GraphPlan();
+    try {
+        P->op = &op;
+        P->ntile = ntile;
+        P->precision = so.precision;
+        P->precond = so.precond;
+        P->nu = so.smooth > 0 ? so.smooth : 2;
+        P->omega = so.omega > 0.0 ? (float)so.omega : 0.7f;
+        const MeshLevel& m0 = c->meshes[op.mesh];
+        const int nd = so.precond == MG_PRECOND_MULTIGRID ? (int)op.mg.size() : 1;
+        for (int d = 0; d < nd; ++d) {
+            const MgDepth& md = *op.mg[d];
+            const MeshLevel& mm = c->meshes[md.mesh];
+            Depth D = {};
+            D.n = (int)md.n;
+            D.W = md.W;
+            D.nrb = (D.n + RBS - 1) / RBS;
+            D.col = mm.ell_col.as<int32_t>();
+            D.L64 = md.L64.as<double>();
+            D.M64 = md.M64.as<double>();
+            D.L32 = md.L32.as<float>();
+            D.LD32 = md.LD32.as<float>();
+            D.dinv32 = md.dinv32.as<float>();
+            if (d + 1 < nd) {
+                D.par = mm.par.as<int32_t>();
+                D.pw = mm.pw.as<float>();
+                D.rt_W = mm.rt_W;
+                D.rt_col = mm.rt_col.as<int32_t>();
+                D.rt_w = mm.rt_w.as<float>();
+            }
+            const size_t e = (size_t)ntile * D.n * G;
+            D.x = (float*)alloc(*P, e * 4);
+            if (so.precond == MG_PRECOND_MULTIGRID && d + 1 < nd) {
+                D.sa = (float*)alloc(*P, e * 4);
+                D.sb = (float*)alloc(*P, e * 4);
+                D.y = (float*)alloc(*P, e * 4);
+            }
+            if (d > 0) D.r = (float*)alloc(*P, e * 4);
+            P->depth.push_back(D);
+        }
+        const size_t e0 = (size_t)ntile * m0.n * G;
+        P->x64 = (double*)alloc(*P, e0 * 8);
+        if (so.precision == MG_FP64) {
+            P->r64 = (double*)alloc(*P, e0 * 8);
+            P->p64 = (double*)alloc(*P, e0 * 8);
+            P->q64 = (double*)alloc(*P, e0 * 8);
+        } else {
+            P->b64 = (double*)alloc(*P, e0 * 8);
+            P->d32 = (float*)alloc(*P, e0 * 4);
+            P->r32 = (float*)alloc(*P, e0 * 4);
+            P->p32 = (float*)alloc(*P, e0 * 4);
+            P->q32 = (float*)alloc(*P, e0 * 4);
+        }
+        const int kpad = ntile * G;
+        P->cols.ensure((size_t)kpad * (6 * sizeof(double) + 3 * sizeof(int)) + 64);
+        char* cb = (char*)P->cols.p;
+        P->st.bb = (double*)cb;
+        P->st.gam = P->st.bb + kpad;
+        P->st.beta = P->st.gam + kpad;
+        P->st.alpha = P->st.beta + kpad;
+        P->st.ref = P->st.alpha + kpad;
+        P->st.prev = P->st.ref + kpad;
+        P->st.act = (int*)(P->st.prev + kpad);
+        P->st.outer = P->st.act + kpad;
+        P->st.iters = P->st.outer + kpad;
+        P->st.ctr = P->st.iters + kpad;
+        const int nrb0 = P->depth[0].nrb;
+        P->part.ensure((size_t)2 * ntile * std::max(nrb0, 1) * G * sizeof(double));
+        P->args.ensure(sizeof(CallArgs));
+        // ---- capture
+        MG_CUDA(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+        MG_CUDA(cudaStreamCreateWithFlags(&P->cap2, cudaStreamNonBlocking));
+        MG_CUDA(cudaStreamCreateWithFlags(&P->cap3, cudaStreamNonBlocking));
+        MG_CUDA(cudaGraphCreate(&P->graph, 0));
+        cudaStream_t s = P->cap;
+        MG_CUDA(cudaStreamBeginCaptureToGraph(s, P->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        const CallArgs* ca = P->args.as<CallArgs>();
+        Depth& D0 = P->depth[0];
+        double* part = P->part.as<double>();
+        double* part2 = part + (size_t)ntile * nrb0 * G;
+        const double inv_dt = 1.0 / op.dt;
+        const double J0 = c->pwm.J0;
+        if (so.precision == MG_FP64) {
+            cudaGraphConditionalHandle h = new_handle(s);
+            kb_init<0><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, P->r64, P->p64,
+                                                         P->q64, nullptr, D0.x, part, part2);
+            kb_scalar_init0<<<1, NSB, 0, s>>>(P->st, part, part2, nrb0, kpad, ca, h);
+            cudaGraph_t body = add_while(s, h);
+            kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
+            kb_scalar_final<<<1, NSB, 0, s>>>(P->st, kpad, ca, 0, (unsigned long long*)c->counters.p,
+                                              (int*)((char*)c->counters.p + 8));
+            MG_CUDA(cudaStreamEndCapture(s, &P->graph));
+            MG_CUDA(cudaStreamBeginCaptureToGraph(P->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            capture_pcg_body<double>(*P, P->cap2, P->x64, P->r64, P->p64, P->q64, D0.L64, ca, 0, h);
+            MG_CUDA(cudaStreamEndCapture(P->cap2, &body));
+        } else {
+            cudaGraphConditionalHandle ho = new_handle(s);
+            kb_init<1><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, nullptr,
+                                                         nullptr, nullptr, P->b64, D0.x, part, part2);
+            kb_scalar_init1<<<1, NSB, 0, s>>>(P->st, part, nrb0, kpad, ca, ho);
+            cudaGraph_t outer = add_while(s, ho);
+            kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
+            kb_scalar_final<<<1, NSB, 0, s>>>(P->st, kpad, ca, 1, (unsigned long long*)c->counters.p,
+                                              (int*)((char*)c->counters.p + 8));
+            MG_CUDA(cudaStreamEndCapture(s, &P->graph));
+            cudaStream_t s2 = P->cap2;
+            MG_CUDA(cudaStreamBeginCaptureToGraph(s2, outer, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            cudaGraphConditionalHandle hi = new_handle(s2);
+            kb_refine_r<<<grid(ntile, nrb0), NTB, 0, s2>>>(D0, P->b64, P->x64, P->r32, P->d32, P->p32, P->q32,
+                                                           P->st.outer, part);
+            kb_scalar_refine<<<1, NSB, 0, s2>>>(P->st, part, nrb0, kpad, ca, hi, ho);
+            cudaGraph_t inner = add_while(s2, hi);
+            kb_update_x<<<grid(ntile, nrb0), NTB, 0, s2>>>(D0, P->x64, P->d32, P->st.outer);
+            MG_CUDA(cudaStreamEndCapture(s2, &outer));
+            MG_CUDA(cudaStreamBeginCaptureToGraph(P->cap3, inner, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            capture_pcg_body<float>(*P, P->cap3, P->d32, P->r32, P->p32, P->q32, D0.L32, ca, 1, hi);
+            MG_CUDA(cudaStreamEndCapture(P->cap3, &inner));
+        }
+        MG_CUDA(cudaGraphInstantiate(&P->exec, P->graph, 0));
+        return P;
+    } catch (...) {
+        cudaStreamCaptureStatus cs;
+        for (cudaStream_t s : {P->cap, P->cap2, P->cap3})
+            if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t junk = nullptr;
+                cudaStreamEndCapture(s, &junk);
+                if (junk && junk != P->graph) cudaGraphDestroy(junk);
+            }
+        cudaGetLastError();
+        delete P;
+        throw;
+    }
+}
+
+}  // namespace
+
+// Batched step through the graph path.  The plan (buffers + instantiated graph) is
+// built on first use for (operator, tile count, form, preconditioner) and reused.
+void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so, SolveCounters* counters) {
+    const int ntile = (io.k + G - 1) / G;
+    GraphPlan* P = nullptr;
+    for (auto* q : c->plans)
+        if (q->op == &op && q->ntile == ntile && q->precision == so.precision && q->precond == so.precond &&
+            q->nu == (so.smooth > 0 ? so.smooth : 2) && q->omega == (so.omega > 0.0 ? (float)so.omega : 0.7f)) {
+            P = q;
+            break;
+        }
+    if (!P) {
+        c->counters.ensure(16);
+        P = build_plan(c, op, ntile, so);
+        c->plans.push_back(P);
+    }
+    CallArgs a = {};
+    a.xprev = io.xprev;
+    a.ld_prev = io.ld_prev;
+    a.g = io.g;
+    a.ld_g = io.ld_g;
+    a.guess = io.guess;
+    a.ld_guess = io.ld_guess;
+    a.xout = io.xout;
+    a.ld_out = io.ld_out;
+    a.signs = io.signs;
+    a.t0 = io.t0;
+    a.tstride = io.tstride;
+    a.k = io.k;
+    const double tol = so.precision == MG_FP64 ? so.cg_tol : so.refine_tol;
+    a.tol2 = tol * tol;
+    a.inner_tol2 = so.inner_tol * so.inner_tol;
+    a.max_it = so.max_cg;
+    a.max_refine = so.max_refine;
+    MG_CUDA(cudaMemcpyAsync(P->args.p, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
+    MG_CUDA(cudaGraphLaunch(P->exec, c->stream));
+    if (counters) {
+        counters->step_solves += io.k;
+        counters->batched_steps += 1;
+        counters->launches += 1;
+    }
+}

@@ -123,6 +123,9 @@ struct Transfer {
     DBuf PT_rowsum_inv;          // n_c: 1 / (P^T 1)
 };
 
+struct GraphPlan;
+void graph_plan_delete(GraphPlan* p);
+
 struct mg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -146,6 +149,7 @@ struct mg_ctx {
     DBuf counters;     // device: [u64 PCG iteration sum][i32 worst status]
     DBuf flag;         // int32 error flag
     DBuf solve_buf[16];  // MGRIT level storage
+    std::vector<GraphPlan*> plans;  // graph-path step plans (buffers + instantiated graphs)
     ~mg_ctx();
 };
 
@@ -186,3 +190,7 @@ struct SolveCounters {
 // `counters` (host, may be null) counts launches and column-steps.
 void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so,
                SolveCounters* counters);
+// Graph path (batch.cu): one kernel per phase over all tiles, loop in a CUDA graph.
+void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so,
+                     SolveCounters* counters);
+void ctx_drop_plans(mg_ctx* c);

@@ -43,7 +43,13 @@ void DBuf::ensure(size_t nbytes) {
     bytes = nbytes;
 }
 
+void ctx_drop_plans(mg_ctx* c) {
+    for (auto* p : c->plans) graph_plan_delete(p);
+    c->plans.clear();
+}
+
 mg_ctx::~mg_ctx() {
+    ctx_drop_plans(this);
     for (auto* o : ops) delete o;
     for (auto& t : transfers) delete t.second;
 }
@@ -773,6 +779,7 @@ mg_status mg_set_material(mg_ctx* c, int32_t region, double sigma, double nu, in
         m.set = true;
         c->finalized = false;
         for (auto& mm : c->meshes) mm.assembled = false;
+        ctx_drop_plans(c);
         for (auto* o : c->ops) delete o;
         c->ops.clear();
     });

@@ -1,0 +1,109 @@
+// Vector loads/stores of work vectors and the ELL row product, shared by the
+// step-solver kernels.  Work vectors are written by other CTAs between phases
+// that are separated by barriers with acquire semantics (cluster barriers, or
+// kernel boundaries), so loads either bypass L1 (ld.global.cg, the default) or
+// are ordinary L1-cached loads (MG_L1 = 1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#ifndef MG_L1
+#define MG_L1 0
+#endif
+
+namespace mgv {
+
+constexpr int WMAX = 8;  // ELL entries handled fully unrolled; wider rows loop
+
+template <class T, int V>
+struct VT;
+template <>
+struct VT<float, 1> { using t = float; };
+template <>
+struct VT<float, 2> { using t = float2; };
+template <>
+struct VT<float, 4> { using t = float4; };
+template <>
+struct VT<double, 1> { using t = double; };
+template <>
+struct VT<double, 2> { using t = double2; };
+
+template <class T, int V>
+__device__ __forceinline__ void vld(const T* p, T (&o)[V]) {
+    if constexpr (std::is_same<T, double>::value && V == 4) {
+        double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+        double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+        o[0] = a.x;
+        o[1] = a.y;
+        o[2] = b.x;
+        o[3] = b.y;
+    } else {
+#if MG_L1
+        typename VT<T, V>::t v = *reinterpret_cast<const typename VT<T, V>::t*>(p);
+#else
+        typename VT<T, V>::t v = __ldcg(reinterpret_cast<const typename VT<T, V>::t*>(p));
+#endif
+        const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int q = 0; q < V; ++q) o[q] = e[q];
+    }
+}
+
+template <class T, int V>
+__device__ __forceinline__ void vst(T* p, const T (&o)[V]) {
+    if constexpr (std::is_same<T, double>::value && V == 4) {
+        __stcg(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
+        __stcg(reinterpret_cast<double2*>(p) + 1, make_double2(o[2], o[3]));
+    } else {
+        typename VT<T, V>::t v;
+        T* e = reinterpret_cast<T*>(&v);
+#pragma unroll
+        for (int q = 0; q < V; ++q) e[q] = o[q];
+#if MG_L1
+        *reinterpret_cast<typename VT<T, V>::t*>(p) = v;
+#else
+        __stcg(reinterpret_cast<typename VT<T, V>::t*>(p), v);
+#endif
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+template <class T>
+__device__ __forceinline__ void stcg(T* p, T v) { __stcg(p, v); }
+
+// acc[e] = sum_w val[w, i] * v[col[w, i]][c0 + e]  (v tile-major with KT columns)
+template <int KT, int V, class A, class VAL, class X>
+__device__ __forceinline__ void ell_vec(const int32_t* __restrict__ col, const VAL* __restrict__ val, int n, int W,
+                                        int i, const X* v, int c0, A (&acc)[V]) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) acc[e] = 0;
+    int32_t j[WMAX];
+    VAL a[WMAX];
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < W) {
+            j[w] = __ldg(col + w * n + i);
+            a[w] = __ldg(val + w * n + i);
+        }
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < W) {
+            X xv[V];
+            vld<X, V>(v + j[w] * KT + c0, xv);
+#pragma unroll
+            for (int e = 0; e < V; ++e) acc[e] += (A)a[w] * (A)xv[e];
+        }
+    for (int w = WMAX; w < W; ++w) {
+        X xv[V];
+        vld<X, V>(v + __ldg(col + w * n + i) * KT + c0, xv);
+        const A aw = (A)__ldg(val + w * n + i);
+#pragma unroll
+        for (int e = 0; e < V; ++e) acc[e] += aw * (A)xv[e];
+    }
+}
+
+}  // namespace mgv

@@ -44,6 +44,7 @@ class mg_solver_opts(C.Structure):
         ("precond", C.c_int),
         ("smooth", C.c_int),
         ("omega", C.c_double),
+        ("path", C.c_int),
     ]
 
 

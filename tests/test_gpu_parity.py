@@ -75,9 +75,10 @@ def test_pwm_table_bit_exact(meshes, N, T, fc, kind):
 
 # ------------------------------------------------------------------ one batched step
 
-@pytest.mark.parametrize("level,k", [(0, 1), (0, 16), (0, 37), (1, 8), (1, 100)])
+@pytest.mark.parametrize("level,k", [(0, 1), (0, 16), (0, 37), (1, 8), (1, 100), (2, 70)])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batched_step(meshes, lin5k, level, k, precision):
+@pytest.mark.parametrize("path", [1, 2])
+def test_batched_step(meshes, lin5k, level, k, precision, path):
     model, ctx, ids = lin5k
     N, T = 256, 5e-3
     fe = fem.FEModel(meshes[level], model)
@@ -90,7 +91,7 @@ def test_batched_step(meshes, lin5k, level, k, precision):
     phi = stepper.LinearPhi(fe, dt_mult * T / N, stepper.Forcing(fe.F, model.pwm.J0, signs, 1))
     want = np.stack([phi(x_in[:, c], i0 + c * istride) for c in range(k)], axis=1)
     out = torch.zeros((n, k), dtype=torch.float64, device="cuda")
-    so = api.solver_opts(precision=precision, cg_tol=1e-14, refine_tol=1e-14)
+    so = api.solver_opts(precision=precision, cg_tol=1e-14, refine_tol=1e-14, path=path)
     _, st = ctx.mg_step(ids[level], N, T, dev(x_in), out, dt_mult=dt_mult, i0=i0, istride=istride, solver=so)
     got = out.cpu().numpy()
     err = np.linalg.norm(got - want, axis=0) / np.linalg.norm(want, axis=0)
@@ -112,13 +113,28 @@ def test_step_rejects_bad_arguments(meshes, lin5k):
         ctx.mg_step(ids[0], 16, 1e-3, x, x, solver=api.solver_opts(tile=3))
 
 
-def test_step_iteration_limit_is_reported(meshes, lin5k):
+@pytest.mark.parametrize("path", [1, 2])
+def test_step_iteration_limit_is_reported(meshes, lin5k, path):
     model, ctx, ids = lin5k
     n = ctx.mg_num_dofs(ids[1])
     x_in = dev(0.01 * np.random.default_rng(0).standard_normal((n, 8)))
     out = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
-    rc, st = ctx.mg_step(ids[1], 256, 5e-3, x_in, out, solver=api.solver_opts(max_cg=3), allow=(-5,))
+    rc, st = ctx.mg_step(ids[1], 256, 5e-3, x_in, out, solver=api.solver_opts(max_cg=3, path=path), allow=(-5,))
     assert rc == -5 and st["worst_status"] == "MG_ECG_MAXIT"
+
+
+def test_step_paths_agree(meshes, lin5k):
+    """Cluster and graph paths compute the same step (different reduction orders)."""
+    model, ctx, ids = lin5k
+    n = ctx.mg_num_dofs(ids[2])
+    x_in = dev(0.01 * np.random.default_rng(4).standard_normal((n, 48)))
+    outs = []
+    for path in (1, 2):
+        out = torch.zeros((n, 48), dtype=torch.float64, device="cuda")
+        ctx.mg_step(ids[2], 4096, 20e-3, x_in, out, i0=1, istride=3, solver=api.solver_opts(path=path))
+        outs.append(out.cpu().numpy())
+    err = np.linalg.norm(outs[0] - outs[1], axis=0) / np.linalg.norm(outs[0], axis=0)
+    assert err.max() <= 1e-11
 
 
 # ------------------------------------------------------------------ sequential stepping
@@ -224,6 +240,18 @@ def test_three_level_vcycle_with_sc(meshes, lin5k):
     _, hist = P.mgrit(gamma=1, tol=1e-12, max_iter=4)
     h = np.array(st["res_hist"][:4])
     assert np.all(np.abs(h - np.array(hist[:4])) <= 1e-6 * np.array(hist[:4]))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mgrit_on_the_graph_path(meshes, lin5k, precision):
+    """64 intervals per batched step: the fine level runs on the graph path."""
+    model, ctx, ids = lin5k
+    N, T = 1024, 5e-3
+    ref = MachineProblem(meshes, model, N, T, (0,), ()).sequential()
+    so = api.solver_opts(precision=precision)
+    opts = api.mgrit_opts(levels=2, m=(16,), space_level=(ids[0], ids[0]), relax=1, tol=1e-9, solver=so)
+    got, st = run_mgrit(ctx, N, T, ref.shape[1], opts)
+    assert rel_err_per_point(got, ref).max() <= (1e-9 if precision == 0 else 1e-6)
 
 
 def test_mixed_precision_mgrit(meshes, lin5k):
