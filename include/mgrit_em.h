@@ -128,7 +128,7 @@ typedef enum { MG_PRECOND_JACOBI = 0, MG_PRECOND_MULTIGRID = 1 } mg_precond;
  * (full-GPU throughput for many columns); MG_PATH_AUTO picks the graph path from
  * MG_GRAPH_MIN_COLUMNS columns on.  Both compute the same step. */
 typedef enum { MG_PATH_AUTO = 0, MG_PATH_CLUSTER = 1, MG_PATH_GRAPH = 2 } mg_path;
-#define MG_GRAPH_MIN_COLUMNS 64
+#define MG_GRAPH_MIN_COLUMNS 16
 
 typedef struct {
     /* linear solver of one backward-Euler step: batched PCG, preconditioned by
@@ -140,7 +140,8 @@ typedef struct {
     int max_cg;         /* iteration limit of one (inner) PCG                              */
     int max_refine;     /* FP32+refinement: limit of outer sweeps                          */
     int precision;      /* mg_precision                                                    */
-    int cluster;        /* CTAs per cluster (1..16; above 8 needs non-portable clusters), 0 = default 8 */
+    int cluster;        /* CTAs per cluster (1..16; above 8 needs non-portable clusters), 0 = library
+                           choice (16 for a single column tile when the device allows it, else 8) */
     int tile;           /* columns per cluster (1, 8, 16, 32), 0 = library choice          */
     int precond;        /* mg_precond                                                      */
     int smooth;         /* damped-Jacobi sweeps before and after each coarse correction    */

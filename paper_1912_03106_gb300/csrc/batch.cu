@@ -18,11 +18,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "internal.h"
+// Phases are separate kernels here, so L1-cached loads of work vectors are coherent.
+#define MG_L1 1
 #include "vec.cuh"
 
 namespace {
@@ -109,6 +112,17 @@ __device__ __forceinline__ double col_total(const double* part, int nrb, int gc)
     return s;
 }
 
+// Column totals with TPC threads per column (TPC a power of two <= 32, consecutive
+// lanes): each thread adds every TPC-th row block, then a fixed shuffle tree.
+// All TPC threads of a column return the total.
+__device__ __forceinline__ double col_total_par(const double* part, int nrb, int gc, int tpc, int sub) {
+    const int t = gc / G, l = gc % G;
+    double s = 0.0;
+    for (int rb = sub; rb < nrb; rb += tpc) s += part[((size_t)t * nrb + rb) * G + l];
+    for (int off = 1; off < tpc; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
+}
+
 template <class T>
 __device__ __forceinline__ T* tv(T* base, int n, int t) { return base + (size_t)t * n * G; }
 
@@ -118,7 +132,7 @@ template <int MODE>
 __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restrict__ ca, double inv_dt,
                                                const double* __restrict__ F, double J0, double* x64, double* r64,
                                                double* p64, double* q64, double* b64, float* z, double* part_bb,
-                                               double* part_rr) {
+                                               double* part_rr, float* r32s) {
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
@@ -158,6 +172,7 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
         if (MODE == 0) {
             const double ri = bi - lx;
             r64[o] = ri;
+            r32s[o] = (float)ri;
             p64[o] = 0.0;
             q64[o] = 0.0;
             rr[0] += ri * ri;
@@ -193,7 +208,7 @@ constexpr int NSB = 1024;
 // FP64 form: ||b||^2, ||r0||^2 -> active columns, loop condition.
 __global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* part_bb, const double* part_rr, int nrb,
                                                       int kpad, const CallArgs* __restrict__ ca,
-                                                      cudaGraphConditionalHandle h) {
+                                                      cudaGraphConditionalHandle h, int use_cond) {
     int any = 0;
     for (int c = threadIdx.x; c < kpad; c += NSB) {
         const double bb = col_total(part_bb, nrb, c), rr = col_total(part_rr, nrb, c);
@@ -208,13 +223,14 @@ __global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* pa
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
         st.ctr[0] = 0;
-        cudaGraphSetConditional(h, (any && ca->max_it > 0) ? 1u : 0u);
+        if (use_cond) cudaGraphSetConditional(h, (any && ca->max_it > 0) ? 1u : 0u);
     }
 }
 
 // FP32+refinement: ||b||^2, every column starts in the refinement loop.
 __global__ void __launch_bounds__(NSB) kb_scalar_init1(Cols st, const double* part_bb, int nrb, int kpad,
-                                                      const CallArgs* __restrict__ ca, cudaGraphConditionalHandle h) {
+                                                      const CallArgs* __restrict__ ca, cudaGraphConditionalHandle h,
+                                                      int use_cond) {
     for (int c = threadIdx.x; c < kpad; c += NSB) {
         st.bb[c] = col_total(part_bb, nrb, c);
         st.outer[c] = c < ca->k;
@@ -223,47 +239,61 @@ __global__ void __launch_bounds__(NSB) kb_scalar_init1(Cols st, const double* pa
     }
     if (threadIdx.x == 0) {
         st.ctr[1] = 0;
-        cudaGraphSetConditional(h, 1u);
+        if (use_cond) cudaGraphSetConditional(h, 1u);
     }
+}
+
+// threads per column for a one-block scalar kernel over kpad columns
+__device__ __forceinline__ int tpc_for(int kpad) {
+    int t = 1;
+    while (t < 32 && t * 2 * kpad <= NSB) t *= 2;
+    return t;
 }
 
 // (r, z) -> gamma, beta
 __global__ void __launch_bounds__(NSB) kb_scalar_gamma(Cols st, const double* part, int nrb, int kpad) {
     const int first = st.ctr[0] == 0;
-    for (int c = threadIdx.x; c < kpad; c += NSB) {
-        const double gn = col_total(part, nrb, c);
-        st.beta[c] = (first || st.gam[c] == 0.0) ? 0.0 : gn / st.gam[c];
-        st.gam[c] = gn;
+    const int tpc = tpc_for(kpad), sub = threadIdx.x % tpc;
+    for (int c = threadIdx.x / tpc; c < kpad; c += NSB / tpc) {
+        const double gn = col_total_par(part, nrb, c, tpc, sub);
+        if (sub == 0) {
+            st.beta[c] = (first || st.gam[c] == 0.0) ? 0.0 : gn / st.gam[c];
+            st.gam[c] = gn;
+        }
     }
 }
 
 // (p, q) -> alpha
 __global__ void __launch_bounds__(NSB) kb_scalar_alpha(Cols st, const double* part, int nrb, int kpad) {
-    for (int c = threadIdx.x; c < kpad; c += NSB) {
-        const double pq = col_total(part, nrb, c);
-        st.alpha[c] = (st.act[c] && pq != 0.0) ? st.gam[c] / pq : 0.0;
+    const int tpc = tpc_for(kpad), sub = threadIdx.x % tpc;
+    for (int c = threadIdx.x / tpc; c < kpad; c += NSB / tpc) {
+        const double pq = col_total_par(part, nrb, c, tpc, sub);
+        if (sub == 0) st.alpha[c] = (st.act[c] && pq != 0.0) ? st.gam[c] / pq : 0.0;
     }
 }
 
 // (r, r) -> convergence masks and the loop condition
 __global__ void __launch_bounds__(NSB) kb_scalar_conv(Cols st, const double* part, int nrb, int kpad,
                                                      const CallArgs* __restrict__ ca, int inner,
-                                                     cudaGraphConditionalHandle h) {
+                                                     cudaGraphConditionalHandle h, int use_cond) {
     const double tol2 = inner ? ca->inner_tol2 : ca->tol2;
+    const int tpc = tpc_for(kpad), sub = threadIdx.x % tpc;
     int any = 0;
-    for (int c = threadIdx.x; c < kpad; c += NSB) {
-        if (st.act[c]) {
-            const double rr = col_total(part, nrb, c);
-            st.iters[c] += 1;
-            if (rr <= tol2 * st.ref[c] || !(rr == rr)) st.act[c] = 0;
+    for (int c = threadIdx.x / tpc; c < kpad; c += NSB / tpc) {
+        const double rr = col_total_par(part, nrb, c, tpc, sub);
+        if (sub == 0) {
+            if (st.act[c]) {
+                st.iters[c] += 1;
+                if (rr <= tol2 * st.ref[c] || !(rr == rr)) st.act[c] = 0;
+            }
+            any |= st.act[c];
         }
-        any |= st.act[c];
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
         const int it = st.ctr[0] + 1;
         st.ctr[0] = it;
-        cudaGraphSetConditional(h, (any && it < ca->max_it) ? 1u : 0u);
+        if (use_cond) cudaGraphSetConditional(h, (any && it < ca->max_it) ? 1u : 0u);
     }
 }
 
@@ -271,7 +301,7 @@ __global__ void __launch_bounds__(NSB) kb_scalar_conv(Cols st, const double* par
 __global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* part, int nrb, int kpad,
                                                        const CallArgs* __restrict__ ca,
                                                        cudaGraphConditionalHandle h_inner,
-                                                       cudaGraphConditionalHandle h_outer) {
+                                                       cudaGraphConditionalHandle h_outer, int use_cond) {
     const int sweep = st.ctr[1];
     int any = 0;
     for (int c = threadIdx.x; c < kpad; c += NSB) {
@@ -293,8 +323,8 @@ __global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* p
     if (threadIdx.x == 0) {
         st.ctr[0] = 0;
         st.ctr[1] = sweep + 1;
-        cudaGraphSetConditional(h_inner, (any && ca->max_it > 0) ? 1u : 0u);
-        cudaGraphSetConditional(h_outer, any ? 1u : 0u);
+        if (use_cond) cudaGraphSetConditional(h_inner, (any && ca->max_it > 0) ? 1u : 0u);
+        if (use_cond) cudaGraphSetConditional(h_outer, any ? 1u : 0u);
     }
 }
 
@@ -395,8 +425,8 @@ __global__ void __launch_bounds__(NTB) kb_restrict(Depth D, Depth C, const float
     }
 }
 
-// y = P x_c, x += y
-__global__ void __launch_bounds__(NTB) kb_prolong(Depth D, Depth C) {
+// y = P x_c, x += y  (x_c = sum of `parts` partial vectors pstride apart)
+__global__ void __launch_bounds__(NTB) kb_prolong(Depth D, Depth C, int parts, size_t pstride) {
     ROWS_F(D, t, rb, i) {
         const float* xc = tv(C.x, C.n, t);
         float yv[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -407,6 +437,12 @@ __global__ void __launch_bounds__(NTB) kb_prolong(Depth D, Depth C) {
                 const float wq = __ldg(D.pw + q * D.n + i);
                 float xv[VF];
                 vld<float, VF>(xc + p * G + c0, xv);
+                for (int sp = 1; sp < parts; ++sp) {
+                    float xs[VF];
+                    vld<float, VF>(xc + sp * pstride + p * G + c0, xs);
+#pragma unroll
+                    for (int e = 0; e < VF; ++e) xv[e] += xs[e];
+                }
 #pragma unroll
                 for (int e = 0; e < VF; ++e) yv[e] += wq * xv[e];
             }
@@ -434,38 +470,98 @@ __global__ void __launch_bounds__(NTB) kb_resupdate(Depth D, float* s_base) {
     }
 }
 
-// coarsest level: x = A^-1 r (dense, FP32), 64 rows x one tile per block
+// coarsest level: x = A^-1 r, a dense contraction on the tensor cores.  Warp-level
+// m16n8k8 TF32 MMAs with FP32 accumulation; each operand is split into a TF32 high
+// part and a TF32 remainder and three products (hi*hi + hi*lo + lo*hi) are
+// accumulated, which keeps FP32-level accuracy.  Block: 4 warps = 64 rows x one
+// 16-column tile; a warp owns 16 rows x 16 columns (two n8 fragments).
+__device__ __forceinline__ unsigned tf32_of(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+    hi = tf32_of(x);
+    lo = tf32_of(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int BK = 128;         // K chunk staged in shared memory
+constexpr int BASE_KSPLIT = 4;  // K splits of the dense base solve (partials summed by the prolongation)
+
+// The K range is split over `ks` blocks per output tile (grid = row blocks x tiles
+// x ks); split s writes its partial product to x_base + s * pstride, and the
+// consumer adds the ks partials in order.
 template <class RT>
-__global__ void __launch_bounds__(NTB) kb_base_dense(int n0, const float* __restrict__ A, const RT* r_base,
-                                                     float* x_base, int nrb64) {
-    __shared__ float As[64][33];
-    __shared__ float Rs[32][G];
-    const int t = blockIdx.x / nrb64, ib = blockIdx.x % nrb64;
-    const RT* r = r_base + (size_t)t * n0 * G;
-    const int row = threadIdx.x / 4, cg = (threadIdx.x % 4) * 4;
-    const int i = ib * 64 + row;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int j0 = 0; j0 < n0; j0 += 32) {
-        for (int q = threadIdx.x; q < 64 * 32; q += NTB) {
-            const int rr = q / 32, cc = q % 32;
-            const int gi = ib * 64 + rr, gj = j0 + cc;
-            As[rr][cc] = (gi < n0 && gj < n0) ? __ldg(A + (size_t)gi * n0 + gj) : 0.0f;
+__global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __restrict__ A, const RT* r_base,
+                                                     float* x_base, int ntile, int ks, size_t pstride) {
+    __shared__ __align__(16) float As[64][BK + 4];  // +4: conflict-free fragment reads
+    __shared__ float Bs[BK][G + 8];
+    const int nrb = (n0 + 63) / 64;
+    const int split = blockIdx.x % ks, bt = blockIdx.x / ks;
+    const int t = bt / nrb, ib = bt % nrb;
+    const int kspan = ((n0 + ks - 1) / ks + BK - 1) / BK * BK;
+    const int kbeg = split * kspan, kend = min(n0, kbeg + kspan);
+    x_base += (size_t)split * pstride;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tig = lane & 3;
+    const RT* rb = r_base + (size_t)t * n0 * G;
+    float acc[2][4] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        // stage A[ib*64 .. +64][k0 .. k0+BK) and r[k0 .. k0+BK][0 .. 16)
+        for (int q = threadIdx.x; q < 64 * BK; q += 128) {
+            const int rr = q / BK, kk = q % BK;
+            const int gi = ib * 64 + rr, gk = k0 + kk;
+            As[rr][kk] = (gi < n0 && gk < kend) ? __ldg(A + (size_t)gi * n0 + gk) : 0.0f;
         }
-        for (int q = threadIdx.x; q < 32 * G; q += NTB) {
-            const int jj = q / G, cc = q % G;
-            const int gj = j0 + jj;
-            Rs[jj][cc] = gj < n0 ? (float)r[(size_t)gj * G + cc] : 0.0f;
+        for (int q = threadIdx.x; q < BK * G; q += 128) {
+            const int kk = q / G, cc = q % G;
+            const int gk = k0 + kk;
+            Bs[kk][cc] = gk < kend ? (float)rb[(size_t)gk * G + cc] : 0.0f;
         }
         __syncthreads();
-#pragma unroll 8
-        for (int jj = 0; jj < 32; ++jj) {
-            const float a = As[row][jj];
+#pragma unroll 4
+        for (int kk = 0; kk < BK; kk += 8) {
+            const int ra = warp * 16 + g;
+            unsigned ahi[4], alo[4];
+            split_tf32(As[ra][kk + tig], ahi[0], alo[0]);
+            split_tf32(As[ra + 8][kk + tig], ahi[1], alo[1]);
+            split_tf32(As[ra][kk + tig + 4], ahi[2], alo[2]);
+            split_tf32(As[ra + 8][kk + tig + 4], ahi[3], alo[3]);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[e] += a * Rs[jj][cg + e];
+            for (int f = 0; f < 2; ++f) {
+                unsigned bh0, bl0, bh1, bl1;
+                split_tf32(Bs[kk + tig][f * 8 + g], bh0, bl0);
+                split_tf32(Bs[kk + tig + 4][f * 8 + g], bh1, bl1);
+                mma_tf32(acc[f], ahi, bh0, bh1);
+                mma_tf32(acc[f], ahi, bl0, bl1);
+                mma_tf32(acc[f], alo, bh0, bh1);
+            }
         }
         __syncthreads();
     }
-    if (i < n0) vst<float, 4>(x_base + ((size_t)t * n0 + i) * G + cg, acc);
+    float* xb = x_base + (size_t)t * n0 * G;
+    const int ra = ib * 64 + warp * 16 + g, rb8 = ra + 8;
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+        const int cc = f * 8 + tig * 2;
+        if (ra < n0) {
+            xb[(size_t)ra * G + cc] = acc[f][0];
+            xb[(size_t)ra * G + cc + 1] = acc[f][1];
+        }
+        if (rb8 < n0) {
+            xb[(size_t)rb8 * G + cc] = acc[f][2];
+            xb[(size_t)rb8 * G + cc + 1] = acc[f][3];
+        }
+    }
 }
 
 // coarsest level without a dense inverse, or Jacobi preconditioning: x = w D^-1 r
@@ -490,6 +586,54 @@ __global__ void __launch_bounds__(NTB) kb_jacobi(Depth D, const RT* r_base, floa
 }
 
 // ---------------------------------------------------------------- PCG update phases
+// Exact float -> double conversion with integer instructions: on GB300 the F2F
+// conversion issues on the FP64 pipe, whose rate is a small fraction of FP32's.
+// Normal numbers convert exactly; zero and denormals give (signed) zero, infinities
+// and NaNs are not produced by the preconditioner.
+__device__ __forceinline__ double f2d_int(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long mant = (unsigned long long)(u & 0x7fffffu) << 29;
+    const unsigned long long ex = (unsigned long long)(e + (1023u - 127u)) << 52;
+    return __longlong_as_double((long long)(e ? (sign | ex | mant) : sign));
+}
+
+template <class A, class X>
+__device__ __forceinline__ A widen(X x) { return (A)x; }
+template <>
+__device__ __forceinline__ double widen<double, float>(float x) { return f2d_int(x); }
+
+// ELL row product with the operand widened by widen<A>()
+template <int V, class A, class VAL, class X>
+__device__ __forceinline__ void ell_vec_w(const int32_t* __restrict__ col, const VAL* __restrict__ val, int n, int W,
+                                          int i, const X* v, int c0, A (&acc)[V]) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) acc[e] = 0;
+    int32_t j[WMAX];
+    VAL a[WMAX];
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < W) {
+            j[w] = __ldg(col + w * n + i);
+            a[w] = __ldg(val + w * n + i);
+        }
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < W) {
+            X xv[V];
+            vld<X, V>(v + j[w] * G + c0, xv);
+#pragma unroll
+            for (int e = 0; e < V; ++e) acc[e] += (A)a[w] * widen<A, X>(xv[e]);
+        }
+    for (int w = WMAX; w < W; ++w) {
+        X xv[V];
+        vld<X, V>(v + __ldg(col + w * n + i) * G + c0, xv);
+        const A aw = (A)__ldg(val + w * n + i);
+#pragma unroll
+        for (int e = 0; e < V; ++e) acc[e] += aw * widen<A, X>(xv[e]);
+    }
+}
 template <class T>
 struct VecOf {
     static constexpr int V = std::is_same<T, double>::value ? 2 : 4;
@@ -514,13 +658,13 @@ __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base,
     for (int i = rb * RBS + threadIdx.x / TPR; i < i1; i += RPP) {
         T lz[V], pv[V], qv[V];
         float zv[V];
-        ell_vec<G, V, T>(D.col, Lv, D.n, D.W, i, z, c0, lz);
+        ell_vec_w<V, T>(D.col, Lv, D.n, D.W, i, z, c0, lz);
         vld<float, V>(z + i * G + c0, zv);
         vld<T, V>(p + i * G + c0, pv);
         vld<T, V>(q + i * G + c0, qv);
 #pragma unroll
         for (int e = 0; e < V; ++e) {
-            pv[e] = (T)zv[e] + bt[e] * pv[e];
+            pv[e] = widen<T, float>(zv[e]) + bt[e] * pv[e];
             qv[e] = lz[e] + bt[e] * qv[e];
             pq[e] += (double)pv[e] * (double)qv[e];
         }
@@ -530,10 +674,10 @@ __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base,
     block_partial<V>(pq, part);
 }
 
-// d += alpha p, r -= alpha q, partial (r, r)
+// d += alpha p, r -= alpha q, partial (r, r); FP64 form: also r32 = (float) r for the V-cycle
 template <class T>
 __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, const T* p_base, const T* q_base,
-                                                const double* alpha, double* part) {
+                                                const double* alpha, double* part, float* r32_base) {
     constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
     int t, rb;
     tile_rb(D.nrb, t, rb);
@@ -561,6 +705,12 @@ __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, c
         }
         vst<T, V>(d + i * G + c0, dv);
         vst<T, V>(r + i * G + c0, rv);
+        if (r32_base) {
+            float rf[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) rf[e] = (float)rv[e];
+            vst<float, V>(tv(r32_base, D.n, t) + i * G + c0, rf);
+        }
     }
     block_partial<V>(rr, part);
 }
@@ -621,6 +771,7 @@ struct GraphPlan {
     cudaStream_t cap = nullptr, cap2 = nullptr, cap3 = nullptr;
     double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *b64 = nullptr;
     float *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float* r32s = nullptr;  // FP64 form: FP32 shadow of the residual
     ~GraphPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -669,10 +820,15 @@ void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* 
         kb_restrict<<<grid(P.ntile, C.nrb), NTB, 0, s>>>(D, C, sl ? D.sb : D.sa);
     }
     Depth& B = P.depth[nd - 1];
-    const int nrb64 = (B.n + 63) / 64;
+    const size_t pstride = (size_t)P.ntile * B.n * G;
+    const int ks = nd == 1 ? 1 : BASE_KSPLIT;
+    const int nbg = ((B.n + 63) / 64) * P.ntile * ks;
+    int parts = 1;
     if (P.op->base_inv.p) {
-        if (nd == 1) kb_base_dense<RT><<<P.ntile * nrb64, NTB, 0, s>>>(B.n, P.op->base_inv.as<float>(), rtop, B.x, nrb64);
-        else kb_base_dense<float><<<P.ntile * nrb64, NTB, 0, s>>>(B.n, P.op->base_inv.as<float>(), B.r, B.x, nrb64);
+        if (nd == 1) kb_base_dense<RT><<<nbg, 128, 0, s>>>(B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0);
+        else kb_base_dense<float><<<nbg, 128, 0, s>>>(B.n, P.op->base_inv.as<float>(), B.r, B.x, P.ntile, ks,
+                                                      pstride);
+        parts = ks;
     } else {
         if (nd == 1) kb_jacobi<RT><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, rtop, w, nullptr);
         else kb_jacobi<float><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, B.r, w, nullptr);
@@ -689,7 +845,8 @@ void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* 
     for (int d = nd - 2; d >= 0; --d) {
         Depth& D = P.depth[d];
         Depth& C = P.depth[d + 1];
-        kb_prolong<<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, C);
+        const bool from_base = d + 1 == nd - 1;
+        kb_prolong<<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, C, from_base ? parts : 1, pstride);
         int sl = sel[d];
         kb_resupdate<<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa);
         for (int sw = 0; sw < P.nu; ++sw) {
@@ -705,16 +862,21 @@ void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* 
 // one PCG iteration body (after the preconditioner)
 template <class T>
 void capture_pcg_body(GraphPlan& P, cudaStream_t s, T* d, T* r, T* p, T* q, const T* Lv, const CallArgs* ca,
-                      int inner, cudaGraphConditionalHandle h) {
+                      int inner, cudaGraphConditionalHandle h, int use_cond) {
     Depth& D0 = P.depth[0];
     double* part = P.part.as<double>();
     const int kpad = P.ntile * G;
-    capture_precondition<T>(P, s, r, part);
+    // the V-cycle always reads an FP32 residual: the FP64 form keeps an FP32 shadow of r
+    float* rf = nullptr;
+    if constexpr (std::is_same<T, double>::value) rf = P.r32s;
+    else rf = r;
+    capture_precondition<float>(P, s, rf, part);
     kb_scalar_gamma<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad);
     kb_pcg_a<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
     kb_scalar_alpha<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad);
-    kb_pcg_b<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, d, r, p, q, P.st.alpha, part);
-    kb_scalar_conv<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad, ca, inner, h);
+    kb_pcg_b<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, d, r, p, q, P.st.alpha, part,
+                                                       std::is_same<T, double>::value ? P.r32s : nullptr);
+    kb_scalar_conv<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad, ca, inner, h, use_cond);
 }
 
 // append a WHILE node at the capture's current position; returns its body graph
@@ -776,7 +938,8 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
                 D.rt_w = mm.rt_w.as<float>();
             }
             const size_t e = (size_t)ntile * D.n * G;
-            D.x = (float*)alloc(*P, e * 4);
+            const bool base_split = so.precond == MG_PRECOND_MULTIGRID && d == nd - 1 && nd > 1 && op.base_inv.p;
+            D.x = (float*)alloc(*P, e * 4 * (base_split ? BASE_KSPLIT : 1));
             if (so.precond == MG_PRECOND_MULTIGRID && d + 1 < nd) {
                 D.sa = (float*)alloc(*P, e * 4);
                 D.sb = (float*)alloc(*P, e * 4);
@@ -791,6 +954,7 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             P->r64 = (double*)alloc(*P, e0 * 8);
             P->p64 = (double*)alloc(*P, e0 * 8);
             P->q64 = (double*)alloc(*P, e0 * 8);
+            P->r32s = (float*)alloc(*P, e0 * 4);
         } else {
             P->b64 = (double*)alloc(*P, e0 * 8);
             P->d32 = (float*)alloc(*P, e0 * 4);
@@ -830,21 +994,21 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         if (so.precision == MG_FP64) {
             cudaGraphConditionalHandle h = new_handle(s);
             kb_init<0><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, P->r64, P->p64,
-                                                         P->q64, nullptr, D0.x, part, part2);
-            kb_scalar_init0<<<1, NSB, 0, s>>>(P->st, part, part2, nrb0, kpad, ca, h);
+                                                         P->q64, nullptr, D0.x, part, part2, P->r32s);
+            kb_scalar_init0<<<1, NSB, 0, s>>>(P->st, part, part2, nrb0, kpad, ca, h, 1);
             cudaGraph_t body = add_while(s, h);
             kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
             kb_scalar_final<<<1, NSB, 0, s>>>(P->st, kpad, ca, 0, (unsigned long long*)c->counters.p,
                                               (int*)((char*)c->counters.p + 8));
             MG_CUDA(cudaStreamEndCapture(s, &P->graph));
             MG_CUDA(cudaStreamBeginCaptureToGraph(P->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-            capture_pcg_body<double>(*P, P->cap2, P->x64, P->r64, P->p64, P->q64, D0.L64, ca, 0, h);
+            capture_pcg_body<double>(*P, P->cap2, P->x64, P->r64, P->p64, P->q64, D0.L64, ca, 0, h, 1);
             MG_CUDA(cudaStreamEndCapture(P->cap2, &body));
         } else {
             cudaGraphConditionalHandle ho = new_handle(s);
             kb_init<1><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, nullptr,
-                                                         nullptr, nullptr, P->b64, D0.x, part, part2);
-            kb_scalar_init1<<<1, NSB, 0, s>>>(P->st, part, nrb0, kpad, ca, ho);
+                                                         nullptr, nullptr, P->b64, D0.x, part, part2, nullptr);
+            kb_scalar_init1<<<1, NSB, 0, s>>>(P->st, part, nrb0, kpad, ca, ho, 1);
             cudaGraph_t outer = add_while(s, ho);
             kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
             kb_scalar_final<<<1, NSB, 0, s>>>(P->st, kpad, ca, 1, (unsigned long long*)c->counters.p,
@@ -855,12 +1019,12 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             cudaGraphConditionalHandle hi = new_handle(s2);
             kb_refine_r<<<grid(ntile, nrb0), NTB, 0, s2>>>(D0, P->b64, P->x64, P->r32, P->d32, P->p32, P->q32,
                                                            P->st.outer, part);
-            kb_scalar_refine<<<1, NSB, 0, s2>>>(P->st, part, nrb0, kpad, ca, hi, ho);
+            kb_scalar_refine<<<1, NSB, 0, s2>>>(P->st, part, nrb0, kpad, ca, hi, ho, 1);
             cudaGraph_t inner = add_while(s2, hi);
             kb_update_x<<<grid(ntile, nrb0), NTB, 0, s2>>>(D0, P->x64, P->d32, P->st.outer);
             MG_CUDA(cudaStreamEndCapture(s2, &outer));
             MG_CUDA(cudaStreamBeginCaptureToGraph(P->cap3, inner, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-            capture_pcg_body<float>(*P, P->cap3, P->d32, P->r32, P->p32, P->q32, D0.L32, ca, 1, hi);
+            capture_pcg_body<float>(*P, P->cap3, P->d32, P->r32, P->p32, P->q32, D0.L32, ca, 1, hi, 1);
             MG_CUDA(cudaStreamEndCapture(P->cap3, &inner));
         }
         MG_CUDA(cudaGraphInstantiate(&P->exec, P->graph, 0));
@@ -880,6 +1044,28 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
 }
 
 }  // namespace
+
+// Profiling aid: the FP64-form kernels of the graph path launched directly on the
+// stream for a fixed number of PCG iterations (no graph, no early exit), so that
+// per-kernel profilers can see every launch.  Selected by MGRIT_EM_EAGER=<iterations>.
+static void run_eager_fp64(mg_ctx* c, GraphPlan& P, int iters) {
+    cudaStream_t s = c->stream;
+    const MeshLevel& m0 = c->meshes[P.op->mesh];
+    Depth& D0 = P.depth[0];
+    const int nrb0 = D0.nrb, kpad = P.ntile * G;
+    double* part = P.part.as<double>();
+    double* part2 = part + (size_t)P.ntile * nrb0 * G;
+    const CallArgs* ca = P.args.as<CallArgs>();
+    kb_init<0><<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, 1.0 / P.op->dt, m0.F.as<double>(), c->pwm.J0, P.x64, P.r64,
+                                                   P.p64, P.q64, nullptr, D0.x, part, part2, P.r32s);
+    kb_scalar_init0<<<1, NSB, 0, s>>>(P.st, part, part2, nrb0, kpad, ca, 0, 0);
+    for (int it = 0; it < iters; ++it)
+        capture_pcg_body<double>(P, s, P.x64, P.r64, P.p64, P.q64, D0.L64, ca, 0, 0, 0);
+    kb_final<<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, P.x64);
+    kb_scalar_final<<<1, NSB, 0, s>>>(P.st, kpad, ca, 0, (unsigned long long*)c->counters.p,
+                                      (int*)((char*)c->counters.p + 8));
+    MG_CUDA(cudaGetLastError());
+}
 
 // Batched step through the graph path.  The plan (buffers + instantiated graph) is
 // built on first use for (operator, tile count, form, preconditioner) and reused.
@@ -916,7 +1102,9 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
     a.max_it = so.max_cg;
     a.max_refine = so.max_refine;
     MG_CUDA(cudaMemcpyAsync(P->args.p, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
-    MG_CUDA(cudaGraphLaunch(P->exec, c->stream));
+    const char* eager = getenv("MGRIT_EM_EAGER");
+    if (eager && so.precision == MG_FP64) run_eager_fp64(c, *P, atoi(eager));
+    else MG_CUDA(cudaGraphLaunch(P->exec, c->stream));
     if (counters) {
         counters->step_solves += io.k;
         counters->batched_steps += 1;

@@ -872,9 +872,37 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
     }
 }
 
+// Largest cluster size <= want (16 or 8) that the device can schedule for this kernel.
+template <int KT, int MODE>
+int usable_cluster(int want, size_t stage_bytes) {
+    static int cached[17] = {};
+    if (want <= 8) return want;
+    if (cached[want]) return cached[want];
+    MG_CUDA(cudaFuncSetAttribute(k_phi_batch<KT, MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    MG_CUDA(cudaFuncSetAttribute(k_phi_batch<KT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(stage_bytes, 64 * 1024)));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(want);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = std::max<size_t>(stage_bytes, 64 * 1024);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = want;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_phi_batch<KT, MODE>, &cfg);
+    cudaGetLastError();
+    cached[want] = (e == cudaSuccess && n > 0) ? want : 8;
+    return cached[want];
+}
+
 template <int KT, int MODE>
 void launch_mode(const PcgArgs& a, int csize, size_t stage_bytes, cudaStream_t stream) {
     const int ntile = (a.k + KT - 1) / KT;
+    csize = usable_cluster<KT, MODE>(csize, stage_bytes);
     MG_CUDA(cudaFuncSetAttribute(k_phi_batch<KT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)stage_bytes));
     if (csize > 8) MG_CUDA(cudaFuncSetAttribute(k_phi_batch<KT, MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -919,9 +947,10 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
     }
     const MeshLevel& m0 = c->meshes[op.mesh];
     const int KT = choose_tile(io.k, so.tile);
-    int csize = so.cluster > 0 ? so.cluster : 8;
-    csize = std::max(1, std::min(16, csize));
     const int ntile = (io.k + KT - 1) / KT;
+    // one tile: the largest cluster (latency-bound); several: 8 CTAs so more clusters fit
+    int csize = so.cluster > 0 ? so.cluster : (ntile == 1 ? 16 : 8);
+    csize = std::max(1, std::min(16, csize));
     PcgArgs a = {};
     a.precond = so.precond;
     a.nu = so.smooth > 0 ? so.smooth : 2;

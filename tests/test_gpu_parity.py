@@ -259,7 +259,7 @@ def test_mixed_precision_mgrit(meshes, lin5k):
     N, T = 256, 5e-3
     ref = MachineProblem(meshes, model, N, T, (0,), ()).sequential()
     so = api.solver_opts(precision=1)
-    opts = api.mgrit_opts(levels=2, m=(16,), space_level=(ids[0], ids[0]), relax=1, tol=1e-10, solver=so)
+    opts = api.mgrit_opts(levels=2, m=(16,), space_level=(ids[0], ids[0]), relax=1, tol=1e-9, solver=so)
     got, st = run_mgrit(ctx, N, T, ref.shape[1], opts)
     assert rel_err_per_point(got, ref).max() <= 1e-6
 
