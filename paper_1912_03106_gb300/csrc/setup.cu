@@ -18,6 +18,9 @@
 
 #include "internal.h"
 
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
 // ------------------------------------------------------------------ errors
 
 [[noreturn]] void mg_fail(mg_status st, const std::string& msg) { throw MgError{st, msg}; }
@@ -192,28 +195,46 @@ __global__ void k_dense_aug(int64_t n, const int32_t* __restrict__ rowptr, const
     aug[i * 2 * n + n + i] = 1.0;
 }
 
-__global__ void k_gj_column(int64_t n, int64_t k, const double* __restrict__ aug, double* __restrict__ colk) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) colk[i] = aug[i * 2 * n + k];
-}
-
-__global__ void k_gj_normalize(int64_t n, int64_t k, double* __restrict__ aug, const double* __restrict__ colk,
-                               int* __restrict__ flag) {
-    int64_t j = k + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double piv = colk[k];
-    if (!(piv > 0.0)) {
-        if (j == k) atomicExch(flag, 1);
-        return;
+// Whole Gauss-Jordan sweep on [A | I] in one cooperative launch.  Pivot k
+// needs column k and row k as they stood after pivot k-1; the threads that
+// produce those entries also copy them into ping-pong buffers, so one grid
+// barrier per pivot suffices.  Only columns k..n+k change at pivot k: the
+// columns left of k are already unit vectors and those right of n+k are still
+// untouched identity columns.  Every block reads the same pivot after the
+// barrier, so a non-positive pivot ends all blocks together.
+__global__ void k_gj_sweep(int64_t n, double* __restrict__ aug, double* __restrict__ colbuf,
+                           double* __restrict__ rowbuf, int* __restrict__ flag) {
+    cg::grid_group grid = cg::this_grid();
+    const int64_t W = 2 * n;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = tid; q < n; q += nth) colbuf[q] = aug[q * W];
+    for (int64_t q = tid; q < W; q += nth) rowbuf[q] = aug[q];
+    grid.sync();
+    for (int64_t k = 0; k < n; ++k) {
+        const double* ck = colbuf + (k & 1) * n;
+        const double* rk = rowbuf + (k & 1) * W;
+        double* cn = colbuf + ((k + 1) & 1) * n;
+        double* rn = rowbuf + ((k + 1) & 1) * W;
+        const double piv = rk[k];
+        if (!(piv > 0.0)) {
+            if (tid == 0) atomicExch(flag, 1);
+            return;
+        }
+        if (tid == 0 && k + 1 < n) rn[n + k + 1] = aug[(k + 1) * W + n + k + 1];
+        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+            const double f = ck[i];
+            double* row = aug + i * W;
+            for (int64_t j = k + threadIdx.x; j <= n + k; j += blockDim.x) {
+                const double pk = rk[j] / piv;
+                const double v = (i == k) ? pk : row[j] - f * pk;
+                row[j] = v;
+                if (j == k + 1) cn[i] = v;
+                if (i == k + 1) rn[j] = v;
+            }
+        }
+        grid.sync();
     }
-    if (j < 2 * n) aug[k * 2 * n + j] /= piv;
-}
-
-__global__ void k_gj_eliminate(int64_t n, int64_t k, double* __restrict__ aug, const double* __restrict__ colk) {
-    int64_t j = k + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t i = blockIdx.y;
-    if (j >= 2 * n || i == k) return;
-    double f = colk[i];
-    if (f != 0.0) aug[i * 2 * n + j] -= f * aug[k * 2 * n + j];
 }
 
 __global__ void k_gj_extract(int64_t n, const double* __restrict__ aug, float* __restrict__ inv) {
@@ -479,19 +500,26 @@ static MgDepth* build_depth(mg_ctx* c, int mesh, double dt) {
 static void build_base_inverse(mg_ctx* c, StepOp& o, int mesh, double dt) {
     MeshLevel& m = c->meshes[mesh];
     const int64_t n = m.n;
-    DBuf aug, colk;
+    DBuf aug, buf;
     aug.ensure((size_t)n * 2 * n * sizeof(double));
-    colk.ensure(n * sizeof(double));
+    buf.ensure((size_t)6 * n * sizeof(double));
     cudaStream_t s = c->stream;
     MG_CUDA(cudaMemsetAsync(aug.p, 0, (size_t)n * 2 * n * sizeof(double), s));
     k_dense_aug<<<nblk(n), 256, 0, s>>>(n, m.rowptr.as<int32_t>(), m.col.as<int32_t>(), m.K.as<double>(),
                                        m.M.as<double>(), 1.0 / dt, aug.as<double>());
-    for (int64_t k = 0; k < n; ++k) {
-        k_gj_column<<<nblk(n), 256, 0, s>>>(n, k, aug.as<double>(), colk.as<double>());
-        k_gj_normalize<<<nblk(2 * n - k), 256, 0, s>>>(n, k, aug.as<double>(), colk.as<double>(), c->flag.as<int>());
-        dim3 g(nblk(2 * n - k), (unsigned)n);
-        k_gj_eliminate<<<g, 256, 0, s>>>(n, k, aug.as<double>(), colk.as<double>());
-    }
+    int dev = 0, nsm = 0, per_sm = 0;
+    MG_CUDA(cudaGetDevice(&dev));
+    MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_sweep, 256, 0));
+    if (per_sm < 1) mg_fail(MG_ECUDA, "Gauss-Jordan sweep cannot be resident");
+    unsigned grid = (unsigned)std::min<int64_t>((int64_t)nsm * per_sm, n);
+    double* aug_p = aug.as<double>();
+    double* col_p = buf.as<double>();
+    double* row_p = col_p + 2 * n;
+    int* flag_p = c->flag.as<int>();
+    int64_t n_arg = n;
+    void* args[] = {&n_arg, &aug_p, &col_p, &row_p, &flag_p};
+    MG_CUDA(cudaLaunchCooperativeKernel((const void*)k_gj_sweep, dim3(grid), dim3(256), args, 0, s));
     o.base_inv.ensure((size_t)n * n * sizeof(float));
     k_gj_extract<<<nblk(n * n), 256, 0, s>>>(n, aug.as<double>(), o.base_inv.as<float>());
     MG_CUDA(cudaGetLastError());
