@@ -147,11 +147,17 @@ typedef struct {
     int smooth;         /* damped-Jacobi sweeps before and after each coarse correction    */
     double omega;       /* Jacobi damping factor                                           */
     int path;           /* mg_path                                                         */
+    /* nonlinear steps (meshes with a Brauer-law material, Sec. 5): damped Newton,
+     * each correction J delta = -F solved by the PCG above (FP64 form, multigrid
+     * with per-column Galerkin coarse operators and a banded base solve) */
+    double newton_tol;  /* stop once ||delta|| <= newton_tol ||a + delta|| (full correction taken) */
+    int max_newton;     /* Newton iterations per step; more is MG_ENEWTON                   */
+    int max_halvings;   /* step-length halvings per iteration while ||F|| would grow        */
 } mg_solver_opts;
 
 /* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,
  * inner_tol 1e-5, max_cg 2000, max_refine 30, FP64, multigrid with 2 sweeps
- * of damping 0.7). */
+ * of damping 0.7; newton_tol 1e-8, max_newton 100, max_halvings 40). */
 void mg_solver_defaults(mg_solver_opts* opts);
 
 typedef struct {
@@ -165,6 +171,7 @@ typedef struct {
                                  per column tile, the inner iterations of its slowest column) */
     int32_t worst_status;     /* worst per-column solver status seen               */
     int64_t launches;         /* CUDA kernels the call launched                    */
+    int64_t newton_iters;     /* Newton iterations summed over column-steps (nonlinear meshes) */
 } mg_stats;
 
 /* One batched backward-Euler step on mesh `level` (Eq. discrete_system):
@@ -172,6 +179,10 @@ typedef struct {
  *     (M/dt + K) x = (M/dt) x_in[:, c] + J0 sum_s b_s(t_{i_c}) F_s,
  * with dt = dt_mult * T / N and fine time index i_c = i0 + c * istride
  * (0 <= i_c <= N).  x_out also serves as the initial guess when guess != 0.
+ * On a mesh with a nonlinear material (Sec. 5) K depends on x and the step is
+ * (M/dt)(x - x_in[:, c]) + K(x) x = J0 sum_s b_s F_s, solved by damped Newton
+ * from x_in[:, c] (or from the guess); a column whose Newton iteration fails
+ * reports MG_ENEWTON and keeps its last iterate.
  * Node-major layouts with leading dimensions ld_in, ld_out >= k.
  * stats may be NULL (then the call does not synchronise). */
 mg_status mg_step(mg_ctx* ctx, int level, int64_t N, double T, int64_t dt_mult, int k,

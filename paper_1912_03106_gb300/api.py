@@ -76,6 +76,7 @@ def stats_dict(st: L.mg_stats) -> dict:
         "cg_iters": st.cg_iters,
         "worst_status": L.STATUS.get(st.worst_status, st.worst_status),
         "launches": st.launches,
+        "newton_iters": st.newton_iters,
     }
 
 

@@ -338,6 +338,79 @@ __global__ void __launch_bounds__(NSB) kb_scalar_final(Cols st, int kpad, const 
     }
 }
 
+// Exact float -> double conversion with integer instructions: on GB300 the F2F
+// conversion issues on the FP64 pipe, whose rate is a small fraction of FP32's.
+// Normal numbers convert exactly; zero and denormals give (signed) zero, infinities
+// and NaNs are not produced by the preconditioner.
+__device__ __forceinline__ double f2d_int(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long mant = (unsigned long long)(u & 0x7fffffu) << 29;
+    const unsigned long long ex = (unsigned long long)(e + (1023u - 127u)) << 52;
+    return __longlong_as_double((long long)(e ? (sign | ex | mant) : sign));
+}
+
+template <class A, class X>
+__device__ __forceinline__ A widen(X x) { return (A)x; }
+template <>
+__device__ __forceinline__ double widen<double, float>(float x) { return f2d_int(x); }
+
+// ELL values: one value per entry shared by all columns (PC = false), or per
+// column (PC = true): entry (w, i) of tile t, column c at ((t W n + w n + i) G + c).
+template <bool PC, class VAL>
+__device__ __forceinline__ const VAL* tile_vals(const VAL* p, const Depth& D, int t) {
+    return PC ? p + (size_t)t * D.W * D.n * G : p;
+}
+
+// ELL row product acc[e] = sum_w val[w, i] v[col[w, i]][c0 + e], the operand
+// widened by widen<A>(); val from tile_vals<PC>()
+template <int V, class A, class VAL, class X, bool PC = false>
+__device__ __forceinline__ void ell_vec_w(const int32_t* __restrict__ col, const VAL* __restrict__ val, int n, int W,
+                                          int i, const X* v, int c0, A (&acc)[V]) {
+    constexpr int NV = PC ? V : 1;
+#pragma unroll
+    for (int e = 0; e < V; ++e) acc[e] = 0;
+    int32_t j[WMAX];
+    VAL a[WMAX][NV];
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < W) {
+            j[w] = __ldg(col + w * n + i);
+            if constexpr (PC) vld<VAL, V>(val + ((size_t)w * n + i) * G + c0, a[w]);
+            else a[w][0] = __ldg(val + w * n + i);
+        }
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < W) {
+            X xv[V];
+            vld<X, V>(v + j[w] * G + c0, xv);
+#pragma unroll
+            for (int e = 0; e < V; ++e) acc[e] += (A)a[w][PC ? e : 0] * widen<A, X>(xv[e]);
+        }
+    for (int w = WMAX; w < W; ++w) {
+        X xv[V];
+        vld<X, V>(v + __ldg(col + w * n + i) * G + c0, xv);
+        VAL aw[NV];
+        if constexpr (PC) vld<VAL, V>(val + ((size_t)w * n + i) * G + c0, aw);
+        else aw[0] = __ldg(val + w * n + i);
+#pragma unroll
+        for (int e = 0; e < V; ++e) acc[e] += (A)aw[PC ? e : 0] * widen<A, X>(xv[e]);
+    }
+}
+
+// Jacobi scaling 1/diag of row i for columns c0 .. c0+V-1
+template <bool PC, int V>
+__device__ __forceinline__ void dinv_of(const Depth& D, int t, int i, int c0, float (&d)[V]) {
+    if constexpr (PC) {
+        vld<float, V>(D.dinv32 + ((size_t)t * D.n + i) * G + c0, d);
+    } else {
+        const float x = __ldg(D.dinv32 + i);
+#pragma unroll
+        for (int e = 0; e < V; ++e) d[e] = x;
+    }
+}
+
 // ---------------------------------------------------------------- multigrid phases (FP32, float4 lanes)
 constexpr int VF = 4;
 constexpr int TPRF = G / VF;       // threads per row
@@ -351,19 +424,20 @@ constexpr int RPPF = NTB / TPRF;   // rows per pass
     for (int i = rb * RBS + threadIdx.x / TPRF; i < _i1; i += RPPF)
 
 // x = w D^-1 r, s = r - w (L D^-1) r
-template <class RT>
+template <class RT, bool PC>
 __global__ void __launch_bounds__(NTB) kb_smooth_first(Depth D, const RT* rin_base, float w) {
     ROWS_F(D, t, rb, i) {
         const RT* rin = tv(rin_base, D.n, t);
         RT rv[VF];
         vld<RT, VF>(rin + i * G + c0, rv);
         float acc[VF];
-        ell_vec<G, VF, float>(D.col, D.LD32, D.n, D.W, i, rin, c0, acc);
-        const float di = __ldg(D.dinv32 + i);
+        ell_vec_w<VF, float, float, RT, PC>(D.col, tile_vals<PC>(D.LD32, D, t), D.n, D.W, i, rin, c0, acc);
+        float di[VF];
+        dinv_of<PC>(D, t, i, c0, di);
         float xo[VF], so[VF];
 #pragma unroll
         for (int e = 0; e < VF; ++e) {
-            xo[e] = w * di * (float)rv[e];
+            xo[e] = w * di[e] * (float)rv[e];
             so[e] = (float)rv[e] - w * acc[e];
         }
         vst<float, VF>(tv(D.x, D.n, t) + i * G + c0, xo);
@@ -373,7 +447,7 @@ __global__ void __launch_bounds__(NTB) kb_smooth_first(Depth D, const RT* rin_ba
 
 // x += w D^-1 s; s' = s - w (L D^-1) s if dst is given (not on a level's last sweep);
 // partial (r, x) if rtop is given (last sweep on the finest level)
-template <class RT>
+template <class RT, bool PC>
 __global__ void __launch_bounds__(NTB) kb_smooth(Depth D, const float* src_base, float* dst_base, const RT* rtop_base,
                                                  float w, double* part) {
     double rz[VF] = {0.0, 0.0, 0.0, 0.0};
@@ -384,10 +458,11 @@ __global__ void __launch_bounds__(NTB) kb_smooth(Depth D, const float* src_base,
             float sv[VF], xv[VF];
             vld<float, VF>(src + i * G + c0, sv);
             vld<float, VF>(x + i * G + c0, xv);
-            const float di = __ldg(D.dinv32 + i);
+            float di[VF];
+            dinv_of<PC>(D, t, i, c0, di);
             float xo[VF];
 #pragma unroll
-            for (int e = 0; e < VF; ++e) xo[e] = xv[e] + w * di * sv[e];
+            for (int e = 0; e < VF; ++e) xo[e] = xv[e] + w * di[e] * sv[e];
             vst<float, VF>(x + i * G + c0, xo);
             if (rtop_base) {
                 RT rv[VF];
@@ -397,7 +472,7 @@ __global__ void __launch_bounds__(NTB) kb_smooth(Depth D, const float* src_base,
             }
             if (dst_base) {  // the next residual is needed unless this is the last sweep
                 float acc[VF];
-                ell_vec<G, VF, float>(D.col, D.LD32, D.n, D.W, i, src, c0, acc);
+                ell_vec_w<VF, float, float, float, PC>(D.col, tile_vals<PC>(D.LD32, D, t), D.n, D.W, i, src, c0, acc);
                 float so[VF];
 #pragma unroll
                 for (int e = 0; e < VF; ++e) so[e] = sv[e] - w * acc[e];
@@ -458,11 +533,13 @@ __global__ void __launch_bounds__(NTB) kb_prolong(Depth D, Depth C, int parts, s
 }
 
 // s -= L y
+template <bool PC>
 __global__ void __launch_bounds__(NTB) kb_resupdate(Depth D, float* s_base) {
     ROWS_F(D, t, rb, i) {
         float* s = tv(s_base, D.n, t);
         float acc[VF], sv[VF];
-        ell_vec<G, VF, float>(D.col, D.L32, D.n, D.W, i, tv(D.y, D.n, t), c0, acc);
+        ell_vec_w<VF, float, float, float, PC>(D.col, tile_vals<PC>(D.L32, D, t), D.n, D.W, i, tv(D.y, D.n, t), c0,
+                                               acc);
         vld<float, VF>(s + i * G + c0, sv);
 #pragma unroll
         for (int e = 0; e < VF; ++e) sv[e] -= acc[e];
@@ -565,18 +642,19 @@ __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __rest
 }
 
 // coarsest level without a dense inverse, or Jacobi preconditioning: x = w D^-1 r
-template <class RT>
+template <class RT, bool PC>
 __global__ void __launch_bounds__(NTB) kb_jacobi(Depth D, const RT* r_base, float w, double* part) {
     double rz[VF] = {0.0, 0.0, 0.0, 0.0};
     {
         ROWS_F(D, t, rb, i) {
             RT rv[VF];
             vld<RT, VF>(tv(r_base, D.n, t) + i * G + c0, rv);
-            const float di = __ldg(D.dinv32 + i);
+            float di[VF];
+            dinv_of<PC>(D, t, i, c0, di);
             float xo[VF];
 #pragma unroll
             for (int e = 0; e < VF; ++e) {
-                xo[e] = w * di * (float)rv[e];
+                xo[e] = w * di[e] * (float)rv[e];
                 rz[e] += (double)rv[e] * (double)xo[e];
             }
             vst<float, VF>(tv(D.x, D.n, t) + i * G + c0, xo);
@@ -585,62 +663,103 @@ __global__ void __launch_bounds__(NTB) kb_jacobi(Depth D, const RT* r_base, floa
     if (part) block_partial<VF>(rz, part);
 }
 
-// ---------------------------------------------------------------- PCG update phases
-// Exact float -> double conversion with integer instructions: on GB300 the F2F
-// conversion issues on the FP64 pipe, whose rate is a small fraction of FP32's.
-// Normal numbers convert exactly; zero and denormals give (signed) zero, infinities
-// and NaNs are not produced by the preconditioner.
-__device__ __forceinline__ double f2d_int(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    const unsigned long long mant = (unsigned long long)(u & 0x7fffffu) << 29;
-    const unsigned long long ex = (unsigned long long)(e + (1023u - 127u)) << 52;
-    return __longlong_as_double((long long)(e ? (sign | ex | mant) : sign));
-}
 
-template <class A, class X>
-__device__ __forceinline__ A widen(X x) { return (A)x; }
-template <>
-__device__ __forceinline__ double widen<double, float>(float x) { return f2d_int(x); }
+// Coarsest level with per-column operators: x = A_c^-1 r by the column's banded
+// Cholesky factor A_c = L L^T (FP32, bandwidth u).  One warp per column.  Row i of
+// column c holds, at Lb[(c n + i) stride + k], L[i][i-k] for k = 1..u and 1/L[i][i]
+// at k = 0; Ub holds L[i+k][i] at k >= 1.  The rows are staged through shared
+// memory BAND_CHUNK at a time; the last u solution values live in a ring.
+constexpr int BAND_WARPS = 4;
+constexpr int BAND_CHUNK = 16;
+constexpr int BAND_RING = 128;  // > largest bandwidth
 
-// ELL row product with the operand widened by widen<A>()
-template <int V, class A, class VAL, class X>
-__device__ __forceinline__ void ell_vec_w(const int32_t* __restrict__ col, const VAL* __restrict__ val, int n, int W,
-                                          int i, const X* v, int c0, A (&acc)[V]) {
+template <class RT>
+__global__ void __launch_bounds__(32 * BAND_WARPS) kb_base_band(int n, int u, int stride, const float* __restrict__ Lb,
+                                                              const float* __restrict__ Ub, const RT* r_base,
+                                                              float* x_base) {
+    extern __shared__ float4 band_sm4[];
+    float* band_sm = reinterpret_cast<float*>(band_sm4);
+    __shared__ float ring_sm[BAND_WARPS][BAND_RING];
+    __shared__ float rhs_sm[BAND_WARPS][BAND_CHUNK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gc = blockIdx.x * BAND_WARPS + warp;
+    const int t = gc / G, l = gc % G;
+    float* rows = band_sm + (size_t)warp * BAND_CHUNK * stride;
+    float* ring = ring_sm[warp];
+    float* rhs = rhs_sm[warp];
+    const RT* r = r_base + (size_t)t * n * G + l;
+    float* x = x_base + (size_t)t * n * G + l;
+    for (int pass = 0; pass < 2; ++pass) {
+        const float* F = (pass == 0 ? Lb : Ub) + (size_t)gc * n * stride;
+        const int nchunk = (n + BAND_CHUNK - 1) / BAND_CHUNK;
+        for (int ch = 0; ch < nchunk; ++ch) {
+            // forward: chunks in increasing row order; backward: decreasing
+            const int c = pass == 0 ? ch : nchunk - 1 - ch;
+            const int i0 = c * BAND_CHUNK, nr = min(BAND_CHUNK, n - i0);
+            __syncwarp();
+            const float4* src = reinterpret_cast<const float4*>(F + (size_t)i0 * stride);
+            float4* dst = reinterpret_cast<float4*>(rows);
+            for (int q = lane; q < nr * stride / 4; q += 32) dst[q] = __ldg(src + q);
+            if (lane < nr) rhs[lane] = pass == 0 ? (float)r[(size_t)(i0 + lane) * G] : x[(size_t)(i0 + lane) * G];
+            __syncwarp();
+            for (int qq = 0; qq < nr; ++qq) {
+                const int q = pass == 0 ? qq : nr - 1 - qq;
+                const int i = i0 + q;
+                const float* row = rows + q * stride;
+                float acc = 0.0f;
+                for (int k = 1 + lane; k <= u; k += 32) {
+                    const int j = pass == 0 ? i - k : i + k;
+                    if (j >= 0 && j < n) acc += row[k] * ring[j & (BAND_RING - 1)];
+                }
 #pragma unroll
-    for (int e = 0; e < V; ++e) acc[e] = 0;
-    int32_t j[WMAX];
-    VAL a[WMAX];
-#pragma unroll
-    for (int w = 0; w < WMAX; ++w)
-        if (w < W) {
-            j[w] = __ldg(col + w * n + i);
-            a[w] = __ldg(val + w * n + i);
+                for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                const float v = (rhs[q] - acc) * row[0];
+                if (lane == 0) {
+                    ring[i & (BAND_RING - 1)] = v;
+                    x[(size_t)i * G] = v;
+                }
+                __syncwarp();
+            }
         }
-#pragma unroll
-    for (int w = 0; w < WMAX; ++w)
-        if (w < W) {
-            X xv[V];
-            vld<X, V>(v + j[w] * G + c0, xv);
-#pragma unroll
-            for (int e = 0; e < V; ++e) acc[e] += (A)a[w] * widen<A, X>(xv[e]);
-        }
-    for (int w = WMAX; w < W; ++w) {
-        X xv[V];
-        vld<X, V>(v + __ldg(col + w * n + i) * G + c0, xv);
-        const A aw = (A)__ldg(val + w * n + i);
-#pragma unroll
-        for (int e = 0; e < V; ++e) acc[e] += aw * widen<A, X>(xv[e]);
     }
 }
+
+// PCG start of a Newton correction J delta = -R: columns in Newton state 1 start
+// from delta = 0 with r = -R; all other columns get r = 0 and stay inactive.
+__global__ void __launch_bounds__(NTB) kb_init_pc(Depth D, const double* __restrict__ R, const int* __restrict__ state,
+                                                  double* x64, double* r64, double* p64, double* q64, float* z,
+                                                  double* part_bb, double* part_rr, float* r32s) {
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    const int lc = threadIdx.x % G, gc = t * G + lc;
+    const bool on = state[gc] == 1;
+    double rr[1] = {0.0};
+    const int i1 = min(D.n, (rb + 1) * RBS);
+    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+        const size_t o = ((size_t)t * D.n + i) * G + lc;
+        const double ri = on ? -R[o] : 0.0;
+        x64[o] = 0.0;
+        z[o] = 0.0f;
+        r64[o] = ri;
+        r32s[o] = (float)ri;
+        p64[o] = 0.0;
+        q64[o] = 0.0;
+        rr[0] += ri * ri;
+    }
+    block_partial<1>(rr, part_bb);
+    __syncthreads();
+    block_partial<1>(rr, part_rr);
+}
+
+// ---------------------------------------------------------------- PCG update phases
+
 template <class T>
 struct VecOf {
     static constexpr int V = std::is_same<T, double>::value ? 2 : 4;
 };
 
 // p = z + beta p, q = L z + beta q, partial (p, q)
-template <class T>
+template <class T, bool PC>
 __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base, T* q_base, const double* beta,
                                                 double* part) {
     constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
@@ -658,7 +777,7 @@ __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base,
     for (int i = rb * RBS + threadIdx.x / TPR; i < i1; i += RPP) {
         T lz[V], pv[V], qv[V];
         float zv[V];
-        ell_vec_w<V, T>(D.col, Lv, D.n, D.W, i, z, c0, lz);
+        ell_vec_w<V, T, T, float, PC>(D.col, tile_vals<PC>(Lv, D, t), D.n, D.W, i, z, c0, lz);
         vld<float, V>(z + i * G + c0, zv);
         vld<T, V>(p + i * G + c0, pv);
         vld<T, V>(q + i * G + c0, qv);
@@ -761,6 +880,8 @@ __global__ void __launch_bounds__(NTB) kb_update_x(Depth D, double* x64, const f
 struct GraphPlan {
     const StepOp* op = nullptr;
     int ntile = 0, precision = 0, precond = 1, nu = 2;
+    bool pc = false;   // per-column operators (Newton Jacobians), see graph_plan_pc
+    PcOperator pco{};
     float omega = 0.7f;
     std::vector<DBuf> bufs;
     DBuf args, cols, part;
@@ -794,25 +915,26 @@ void* alloc(GraphPlan& P, size_t bytes) {
 inline unsigned grid(int ntile, int nrb) { return (unsigned)(ntile * nrb); }
 
 // one preconditioner application on the capture stream: z = B r into depth[0].x;
-// the last kernel writes the (r, z) partials into part
-template <class RT>
-void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* part) {
+// the last kernel writes the (r, z) partials into part.  PC: per-column operators
+// at every depth and a per-column banded Cholesky factor on the base depth.
+template <class RT, bool PC>
+void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double* part) {
     const int nd = (int)P.depth.size();
     const float w = P.omega;
     if (P.precond == 0) {
         Depth& D = P.depth[0];
-        kb_jacobi<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, rtop, 1.0f, part);
+        kb_jacobi<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, rtop, 1.0f, part);
         return;
     }
     std::vector<int> sel(nd, 0);
     for (int d = 0; d < nd - 1; ++d) {
         Depth& D = P.depth[d];
-        if (d == 0) kb_smooth_first<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, rtop, w);
-        else kb_smooth_first<float><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, D.r, w);
+        if (d == 0) kb_smooth_first<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, rtop, w);
+        else kb_smooth_first<float, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, D.r, w);
         int sl = 0;
         for (int sw = 1; sw < P.nu; ++sw) {
-            kb_smooth<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr, w,
-                                                              nullptr);
+            kb_smooth<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr, w,
+                                                                  nullptr);
             sl ^= 1;
         }
         sel[d] = sl;
@@ -824,22 +946,26 @@ void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* 
     const int ks = nd == 1 ? 1 : BASE_KSPLIT;
     const int nbg = ((B.n + 63) / 64) * P.ntile * ks;
     int parts = 1;
-    if (P.op->base_inv.p) {
+    if (PC) {
+        const unsigned nb = (unsigned)(P.ntile * G / BAND_WARPS);
+        const size_t smem = (size_t)BAND_WARPS * BAND_CHUNK * P.pco.band_stride * sizeof(float);
+        if (nd == 1) kb_base_band<RT><<<nb, 32 * BAND_WARPS, smem, s>>>(B.n, P.pco.band_u, P.pco.band_stride,
+                                                                       P.pco.band_L, P.pco.band_U, rtop, B.x);
+        else kb_base_band<float><<<nb, 32 * BAND_WARPS, smem, s>>>(B.n, P.pco.band_u, P.pco.band_stride,
+                                                                  P.pco.band_L, P.pco.band_U, B.r, B.x);
+    } else if (P.op->base_inv.p) {
         if (nd == 1) kb_base_dense<RT><<<nbg, 128, 0, s>>>(B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0);
         else kb_base_dense<float><<<nbg, 128, 0, s>>>(B.n, P.op->base_inv.as<float>(), B.r, B.x, P.ntile, ks,
                                                       pstride);
         parts = ks;
     } else {
-        if (nd == 1) kb_jacobi<RT><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, rtop, w, nullptr);
-        else kb_jacobi<float><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, B.r, w, nullptr);
+        if (nd == 1) kb_jacobi<RT, PC><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, rtop, w, nullptr);
+        else kb_jacobi<float, PC><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, B.r, w, nullptr);
     }
     if (nd == 1) {
-        // (r, z) for a single-level hierarchy: a no-op smoothing pass computes it
+        // z is final; a zero-weight sweep accumulates (r, z) for a single-level hierarchy
         Depth& D = P.depth[0];
-        Depth Z = D;
-        Z.x = D.x;
-        // z is final; accumulate (r, z) with a zero-weight sweep
-        kb_smooth<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(Z, D.x, nullptr, rtop, 0.0f, part);
+        kb_smooth<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, D.x, nullptr, rtop, 0.0f, part);
         return;
     }
     for (int d = nd - 2; d >= 0; --d) {
@@ -848,15 +974,22 @@ void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* 
         const bool from_base = d + 1 == nd - 1;
         kb_prolong<<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, C, from_base ? parts : 1, pstride);
         int sl = sel[d];
-        kb_resupdate<<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa);
+        kb_resupdate<PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa);
         for (int sw = 0; sw < P.nu; ++sw) {
             const bool last = sw == P.nu - 1;
             const bool top = last && d == 0;
-            kb_smooth<RT><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa, last ? nullptr : (sl ? D.sa : D.sb),
-                                                              top ? rtop : nullptr, w, top ? part : nullptr);
+            kb_smooth<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa,
+                                                                  last ? nullptr : (sl ? D.sa : D.sb),
+                                                                  top ? rtop : nullptr, w, top ? part : nullptr);
             sl ^= 1;
         }
     }
+}
+
+template <class RT>
+void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* part) {
+    if (P.pc) capture_precondition_t<RT, true>(P, s, rtop, part);
+    else capture_precondition_t<RT, false>(P, s, rtop, part);
 }
 
 // one PCG iteration body (after the preconditioner)
@@ -872,7 +1005,8 @@ void capture_pcg_body(GraphPlan& P, cudaStream_t s, T* d, T* r, T* p, T* q, cons
     else rf = r;
     capture_precondition<float>(P, s, rf, part);
     kb_scalar_gamma<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad);
-    kb_pcg_a<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
+    if (P.pc) kb_pcg_a<T, true><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
+    else kb_pcg_a<T, false><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
     kb_scalar_alpha<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad);
     kb_pcg_b<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, d, r, p, q, P.st.alpha, part,
                                                        std::is_same<T, double>::value ? P.r32s : nullptr);
@@ -906,11 +1040,16 @@ cudaGraphConditionalHandle new_handle(cudaStream_t s) {
     return h;
 }
 
-GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so) {
+GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so,
+                      const PcOperator* pco = nullptr) {
     auto* P = new GraphPlan();
     try {
         P->op = &op;
         P->ntile = ntile;
+        if (pco) {
+            P->pc = true;
+            P->pco = *pco;
+        }
         P->precision = so.precision;
         P->precond = so.precond;
         P->nu = so.smooth > 0 ? so.smooth : 2;
@@ -930,6 +1069,13 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             D.L32 = md.L32.as<float>();
             D.LD32 = md.LD32.as<float>();
             D.dinv32 = md.dinv32.as<float>();
+            if (P->pc) {  // per-column Jacobians replace the step operator's values
+                D.L64 = pco->d[d].J64;
+                D.M64 = nullptr;
+                D.L32 = pco->d[d].J32;
+                D.LD32 = pco->d[d].LD32;
+                D.dinv32 = pco->d[d].dinv32;
+            }
             if (d + 1 < nd) {
                 D.par = mm.par.as<int32_t>();
                 D.pw = mm.pw.as<float>();
@@ -938,7 +1084,8 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
                 D.rt_w = mm.rt_w.as<float>();
             }
             const size_t e = (size_t)ntile * D.n * G;
-            const bool base_split = so.precond == MG_PRECOND_MULTIGRID && d == nd - 1 && nd > 1 && op.base_inv.p;
+            const bool base_split =
+                !P->pc && so.precond == MG_PRECOND_MULTIGRID && d == nd - 1 && nd > 1 && op.base_inv.p;
             D.x = (float*)alloc(*P, e * 4 * (base_split ? BASE_KSPLIT : 1));
             if (so.precond == MG_PRECOND_MULTIGRID && d + 1 < nd) {
                 D.sa = (float*)alloc(*P, e * 4);
@@ -993,11 +1140,15 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         const double J0 = c->pwm.J0;
         if (so.precision == MG_FP64) {
             cudaGraphConditionalHandle h = new_handle(s);
-            kb_init<0><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, P->r64, P->p64,
-                                                         P->q64, nullptr, D0.x, part, part2, P->r32s);
+            if (P->pc)
+                kb_init_pc<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, pco->R, pco->state, P->x64, P->r64, P->p64, P->q64,
+                                                             D0.x, part, part2, P->r32s);
+            else
+                kb_init<0><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, P->r64,
+                                                             P->p64, P->q64, nullptr, D0.x, part, part2, P->r32s);
             kb_scalar_init0<<<1, NSB, 0, s>>>(P->st, part, part2, nrb0, kpad, ca, h, 1);
             cudaGraph_t body = add_while(s, h);
-            kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
+            if (!P->pc) kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
             kb_scalar_final<<<1, NSB, 0, s>>>(P->st, kpad, ca, 0, (unsigned long long*)c->counters.p,
                                               (int*)((char*)c->counters.p + 8));
             MG_CUDA(cudaStreamEndCapture(s, &P->graph));
@@ -1073,7 +1224,7 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
     const int ntile = (io.k + G - 1) / G;
     GraphPlan* P = nullptr;
     for (auto* q : c->plans)
-        if (q->op == &op && q->ntile == ntile && q->precision == so.precision && q->precond == so.precond &&
+        if (!q->pc && q->op == &op && q->ntile == ntile && q->precision == so.precision && q->precond == so.precond &&
             q->nu == (so.smooth > 0 ? so.smooth : 2) && q->omega == (so.omega > 0.0 ? (float)so.omega : 0.7f)) {
             P = q;
             break;
@@ -1110,4 +1261,25 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
         counters->batched_steps += 1;
         counters->launches += 1;
     }
+}
+
+// ---------------------------------------------------------------- per-column systems (Newton corrections)
+GraphPlan* graph_plan_pc(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so, const PcOperator& pco) {
+    if (so.precision != MG_FP64) mg_fail(MG_EINVAL, "Newton corrections are solved in the FP64 form");
+    if (pco.band_u >= BAND_RING) mg_fail(MG_EINVAL, "base mesh bandwidth too large for the banded coarse solve");
+    c->counters.ensure(16);
+    return build_plan(c, op, ntile, so, &pco);
+}
+
+double* graph_plan_solution(GraphPlan* p) { return p->x64; }
+
+void graph_plan_run(mg_ctx* c, GraphPlan* P, int k, const mg_solver_opts& so) {
+    CallArgs a = {};
+    a.k = k;
+    a.tol2 = so.cg_tol * so.cg_tol;
+    a.inner_tol2 = so.inner_tol * so.inner_tol;
+    a.max_it = so.max_cg;
+    a.max_refine = so.max_refine;
+    MG_CUDA(cudaMemcpyAsync(P->args.p, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
+    MG_CUDA(cudaGraphLaunch(P->exec, c->stream));
 }

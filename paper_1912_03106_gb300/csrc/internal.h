@@ -12,6 +12,8 @@
 #include "mgrit_em.h"
 
 #define MG_MAX_REGIONS 64
+#define MG_MAX_DEPTH 6
+#define MG_MAX_DENSE 4096   // largest base mesh inverted densely
 
 struct MgError {
     mg_status st;
@@ -67,6 +69,7 @@ struct PwmSpec {
 // One P1 mesh and its assembled linear operators (interior unknowns only).
 struct MeshLevel {
     int64_t n_nodes = 0, n_tri = 0, n = 0, nnz = 0;
+    int64_t n_nl = 0;           // elements with a nonlinear material law
     std::vector<double> xy;
     std::vector<int32_t> tri, region;
     std::vector<int32_t> node2dof;  // -1 on Dirichlet nodes
@@ -125,6 +128,10 @@ struct Transfer {
 
 struct GraphPlan;
 void graph_plan_delete(GraphPlan* p);
+struct NewtonPlan;
+void newton_plan_delete(NewtonPlan* p);
+struct NlMesh;
+void nl_mesh_delete(NlMesh* p);
 
 struct mg_ctx {
     int device = 0;
@@ -150,11 +157,11 @@ struct mg_ctx {
     DBuf flag;         // int32 error flag
     DBuf solve_buf[16];  // MGRIT level storage
     std::vector<GraphPlan*> plans;  // graph-path step plans (buffers + instantiated graphs)
+    std::vector<NewtonPlan*> nplans;  // Newton-step plans (own their per-column PCG graphs)
+    std::map<int, NlMesh*> nl;       // mesh -> static data of its nonlinear elements
     ~mg_ctx();
 };
 
-#define MG_MAX_DEPTH 6
-#define MG_MAX_DENSE 4096   // largest base mesh inverted densely
 
 // ---- set-up helpers (setup.cu)
 void ctx_finalize(mg_ctx* c);
@@ -181,7 +188,7 @@ struct PhiIO {
 };
 
 struct SolveCounters {
-    int64_t step_solves = 0, batched_steps = 0, cg_iters = 0, launches = 0;
+    int64_t step_solves = 0, batched_steps = 0, cg_iters = 0, launches = 0, newton_iters = 0;
     int32_t worst_status = 0;
 };
 
@@ -194,3 +201,29 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
 void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so,
                      SolveCounters* counters);
 void ctx_drop_plans(mg_ctx* c);
+
+// ---- per-column systems: the graph path's PCG with one operator per column
+// (tile-major storage, 16 columns per tile; see batch.cu)
+constexpr int MG_TILE = 16;
+struct PcDepth {
+    double* J64 = nullptr;   // depth 0 only: FP64 operator of the PCG
+    float* J32 = nullptr;    // FP32 operator of the V-cycle
+    float* LD32 = nullptr;   // J32 scaled by the column's 1/diag of the neighbour row
+    float* dinv32 = nullptr; // 1/diag per row and column
+};
+struct PcOperator {
+    PcDepth d[MG_MAX_DEPTH];
+    const float* band_L = nullptr;  // banded Cholesky factor of the base depth per column
+    const float* band_U = nullptr;
+    int band_u = 0, band_stride = 0;
+    const double* R = nullptr;      // residual: the system solved is J delta = -R
+    const int* state = nullptr;     // only columns with state 1 are solved
+};
+GraphPlan* graph_plan_pc(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so, const PcOperator& pco);
+double* graph_plan_solution(GraphPlan* p);
+void graph_plan_run(mg_ctx* c, GraphPlan* p, int k, const mg_solver_opts& so);
+
+// ---- Newton steps for meshes with nonlinear materials (newton.cu)
+bool mesh_is_nonlinear(const mg_ctx* c, int mesh);
+void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so,
+                      SolveCounters* counters);

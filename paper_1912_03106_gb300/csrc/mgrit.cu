@@ -333,6 +333,7 @@ void fill_stats(mg_ctx* c, const SolveCounters& cnt, mg_stats* st) {
     st->step_solves = cnt.step_solves;
     st->batched_steps = cnt.batched_steps;
     st->launches = cnt.launches;
+    st->newton_iters = cnt.newton_iters;
     if (worst < st->worst_status || st->worst_status == 0) st->worst_status = worst;
 }
 
@@ -561,6 +562,9 @@ void mg_solver_defaults(mg_solver_opts* s) {
     s->precond = MG_PRECOND_MULTIGRID;
     s->smooth = 2;
     s->omega = 0.7;
+    s->newton_tol = 1e-8;
+    s->max_newton = 100;
+    s->max_halvings = 40;
 }
 
 void mg_opts_defaults(mg_opts* o) {

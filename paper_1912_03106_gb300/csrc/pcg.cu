@@ -941,6 +941,10 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
     if (so.max_cg < 1 || so.max_refine < 0 || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) ||
         (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID))
         mg_fail(MG_EINVAL, "bad solver options");
+    if (mesh_is_nonlinear(c, op.mesh)) {
+        phi_batch_newton(c, op, io, so, counters);
+        return;
+    }
     if (so.path == MG_PATH_GRAPH || (so.path == MG_PATH_AUTO && io.k >= MG_GRAPH_MIN_COLUMNS)) {
         phi_batch_graph(c, op, io, so, counters);
         return;
@@ -1118,6 +1122,8 @@ void static_step(void* arg) {
     if (!op || !signs)
         mg_fail(MG_ESTATE, "mg_step_static: the step operator or PWM table for this level, N, T and dt does not exist "
                            "yet; one regular mg_step call with the same arguments builds both");
+    if (mesh_is_nonlinear(c, op->mesh))
+        mg_fail(MG_EINVAL, "mg_step_static: nonlinear (Newton) steps need per-column Jacobian storage; use mg_step");
     const MeshLevel& m0 = c->meshes[op->mesh];
     const int KT = choose_tile(q.k, so.tile);
     const int csize = std::max(1, std::min(16, so.cluster > 0 ? so.cluster : 8));

@@ -47,12 +47,15 @@ void DBuf::ensure(size_t nbytes) {
 }
 
 void ctx_drop_plans(mg_ctx* c) {
+    for (auto* p : c->nplans) newton_plan_delete(p);
+    c->nplans.clear();
     for (auto* p : c->plans) graph_plan_delete(p);
     c->plans.clear();
 }
 
 mg_ctx::~mg_ctx() {
     ctx_drop_plans(this);
+    for (auto& q : nl) nl_mesh_delete(q.second);
     for (auto* o : ops) delete o;
     for (auto& t : transfers) delete t.second;
 }
@@ -416,6 +419,7 @@ static void assemble_mesh(mg_ctx* c, MeshLevel& m) {
     const int64_t nt = m.n_tri;
     std::vector<double> sig(nt), nu(nt), kk(3 * nt);
     std::vector<int32_t> law(nt), esrc(nt);
+    m.n_nl = 0;
     for (int64_t e = 0; e < nt; ++e) {
         int r = m.region[e];
         const Material& mt = c->mats[r];
@@ -426,6 +430,7 @@ static void assemble_mesh(mg_ctx* c, MeshLevel& m) {
         kk[3 * e] = mt.k1;
         kk[3 * e + 1] = mt.k2;
         kk[3 * e + 2] = mt.k3;
+        if (mt.law == 1) m.n_nl++;
         const Source& s = c->srcs[r];
         esrc[e] = s.phase < 0 ? -1 : 2 * s.phase + (s.sign < 0 ? 1 : 0);
     }

@@ -45,6 +45,9 @@ class mg_solver_opts(C.Structure):
         ("smooth", C.c_int),
         ("omega", C.c_double),
         ("path", C.c_int),
+        ("newton_tol", C.c_double),
+        ("max_newton", C.c_int),
+        ("max_halvings", C.c_int),
     ]
 
 
@@ -60,6 +63,7 @@ class mg_stats(C.Structure):
         ("cg_iters", C.c_int64),
         ("worst_status", C.c_int32),
         ("launches", C.c_int64),
+        ("newton_iters", C.c_int64),
     ]
 
 
