@@ -153,11 +153,15 @@ typedef struct {
     double newton_tol;  /* stop once ||delta|| <= newton_tol ||a + delta|| (full correction taken) */
     int max_newton;     /* Newton iterations per step; more is MG_ENEWTON                   */
     int max_halvings;   /* step-length halvings per iteration while ||F|| would grow        */
+    double newton_lin_tol; /* PCG stop of each correction: ||J delta + F|| <= newton_lin_tol ||F||
+                              (an inexact Newton step; the last correction is below newton_tol,
+                              so its relative error does not reach the result)               */
 } mg_solver_opts;
 
 /* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,
  * inner_tol 1e-5, max_cg 2000, max_refine 30, FP64, multigrid with 2 sweeps
- * of damping 0.7; newton_tol 1e-8, max_newton 100, max_halvings 40). */
+ * of damping 0.7; newton_tol 1e-8, max_newton 100, max_halvings 40,
+ * newton_lin_tol 1e-6). */
 void mg_solver_defaults(mg_solver_opts* opts);
 
 typedef struct {

@@ -201,6 +201,9 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
 void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so,
                      SolveCounters* counters);
 void ctx_drop_plans(mg_ctx* c);
+// Diagnostics on stderr, from the environment variable MGRIT_EM_TRACE: 0 off,
+// 1 one line per MGRIT iteration, 2 also one line per batched Newton step.
+int mg_trace_level();
 
 // ---- per-column systems: the graph path's PCG with one operator per column
 // (tile-major storage, 16 columns per tile; see batch.cu)

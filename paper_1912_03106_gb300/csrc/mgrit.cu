@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -505,6 +506,9 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
         S.residual(0);
         double rn = S.read_norm();
         hist.push_back(rn);
+        if (mg_trace_level() >= 1)
+            std::fprintf(stderr, "[mgrit] iteration %d  residual %.4e  %.3f s  step-solves %lld  newton %lld\n", it,
+                         rn, secs(t1, clk::now()), (long long)S.cnt.step_solves, (long long)S.cnt.newton_iters);
         if (it == 0) r0 = rn;
         double ref = o.tol_relative ? r0 : 1.0;
         if (rn <= o.tol * ref) {
@@ -565,6 +569,7 @@ void mg_solver_defaults(mg_solver_opts* s) {
     s->newton_tol = 1e-8;
     s->max_newton = 100;
     s->max_halvings = 40;
+    s->newton_lin_tol = 1e-6;
 }
 
 void mg_opts_defaults(mg_opts* o) {

@@ -4,7 +4,8 @@
 // density, nu(|B|^2) = k1 exp(k2 |B|^2) + k3 with |B|^2 = |grad a|^2, so one step
 // of Eq. discrete_system is the nonlinear system
 //     F(a) = (M/dt)(a - a_prev) + K(a) a - f(t) = 0,
-// solved per column by damped Newton started at a_prev (or at the caller's guess):
+// solved per column by damped Newton started at a_prev (with a caller's guess, at
+// whichever of the guess and a_prev has the smaller residual):
 //     J(a) delta = -F(a),  J(a) = M/dt + sum_T |T| G (nu I + 2 nu' g g^T) G^T,
 // where g = G^T a_T is the element gradient and nu' = d nu / d|B|^2.  The full
 // correction is taken, and the step ends, once ||delta|| <= newton_tol ||a + delta||;
@@ -27,6 +28,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -241,9 +244,17 @@ __global__ void __launch_bounds__(NTB) kn_resid(Step S, int64_t ne, const int32_
     partial_col(aa, part_aa);
 }
 
-// ||F||^2 at the start iterate
-__global__ void kn_first_norm(Cols C, const double* part, int nrb, int kpad) {
-    for (int c = threadIdx.x; c < kpad; c += blockDim.x) C.nr2[c] = col_sum(part, nrb, c);
+// ||F||^2 at the start iterate.  With a guess, the start is whichever of the
+// guess (residual in part_g) and a_prev (residual in part_p) has the smaller
+// residual; accept[c] marks the columns that start from a_prev.
+__global__ void kn_first_norm(Cols C, const double* part_g, const double* part_p, int nrb, int kpad) {
+    for (int c = threadIdx.x; c < kpad; c += blockDim.x) {
+        const double rg = col_sum(part_g, nrb, c);
+        const double rp = part_p ? col_sum(part_p, nrb, c) : rg;
+        const int prev = part_p && rp < rg;
+        C.accept[c] = prev;
+        C.nr2[c] = prev ? rp : rg;
+    }
 }
 
 // Jacobian on the ELL pattern: J = M/dt + Kc + sum_contrib w . N_e  (every column)
@@ -760,8 +771,11 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
                       SolveCounters* counters) {
     if (so.precision != MG_FP64 || so.precond != MG_PRECOND_MULTIGRID)
         mg_fail(MG_EINVAL, "nonlinear steps use the FP64 form with the multigrid preconditioner");
-    if (!(so.newton_tol > 0.0) || so.max_newton < 1 || so.max_halvings < 0)
+    if (!(so.newton_tol > 0.0) || so.max_newton < 1 || so.max_halvings < 0 || !(so.newton_lin_tol > 0.0) ||
+        !(so.newton_lin_tol < 1.0))
         mg_fail(MG_EINVAL, "bad Newton options");
+    mg_solver_opts lin = so;  // the corrections' PCG stops at newton_lin_tol
+    lin.cg_tol = so.newton_lin_tol;
     const int ntile = (io.k + G - 1) / G, kpad = ntile * G;
     NewtonPlan* P = newton_plan(c, op, ntile, so);
     const MeshLevel& m0 = c->meshes[op.mesh];
@@ -774,6 +788,8 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
     double* part_aa = part_rr + (size_t)ntile * nrb0 * G;
     double* part_dd = part_aa + (size_t)ntile * nrb0 * G;
     int64_t launches = 0;
+    int rounds = 0, newton_its = 0;
+    const auto t_start = std::chrono::steady_clock::now();
 
     Step S = {};
     S.n = (int)m0.n;
@@ -807,8 +823,19 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
     kn_elem<0><<<ge, NTB, 0, s>>>(E, P->a, P->cols.state, ST_SOLVE, P->yN);
     kn_resid<<<g0, NTB, 0, s>>>(S, N0.ne, N0.inc_ptr.as<int32_t>(), N0.inc_src.as<int32_t>(), P->yN, P->a, P->aprev,
                                 P->cols.state, ST_SOLVE, P->R, part_rr, part_aa);
-    kn_first_norm<<<1, 1024, 0, s>>>(P->cols, part_rr, nrb0, kpad);
-    launches += 5;
+    launches += 4;
+    if (io.guess) {
+        // residual at a_prev as well: each column starts from the better of the two
+        kn_elem<0><<<ge, NTB, 0, s>>>(E, P->aprev, P->cols.state, ST_SOLVE, P->yN);
+        kn_resid<<<g0, NTB, 0, s>>>(S, N0.ne, N0.inc_ptr.as<int32_t>(), N0.inc_src.as<int32_t>(), P->yN, P->aprev,
+                                    P->aprev, P->cols.state, ST_SOLVE, P->Rt, part_dd, part_aa);
+        kn_first_norm<<<1, 1024, 0, s>>>(P->cols, part_rr, part_dd, nrb0, kpad);
+        kn_accept<<<g0, NTB, 0, s>>>((int)m0.n, nrb0, P->cols.accept, P->a, P->aprev, P->R, P->Rt);
+        launches += 4;
+    } else {
+        kn_first_norm<<<1, 1024, 0, s>>>(P->cols, part_rr, nullptr, nrb0, kpad);
+        launches += 1;
+    }
     const int nd = (int)op.mg.size();
     for (int it = 0; it < so.max_newton; ++it) {
         // Jacobian hierarchy of every column at its current iterate
@@ -851,13 +878,15 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
             launches += 1;
         }
         // Newton correction of the columns in state SOLVE
-        graph_plan_run(c, P->pcg, io.k, so);
+        graph_plan_run(c, P->pcg, io.k, lin);
         launches += 1;
         const double* delta = graph_plan_solution(P->pcg);
         kn_begin_trial<<<1, 1024, 0, s>>>(P->cols, kpad);
         launches += 1;
         bool more = false;
+        ++newton_its;
         for (int h = 0; h <= so.max_halvings; ++h) {
+            ++rounds;
             kn_trial<<<g0, NTB, 0, s>>>((int)m0.n, nrb0, P->a, delta, P->cols, P->at, part_dd);
             kn_elem<0><<<ge, NTB, 0, s>>>(E, P->at, P->cols.state, ST_TRIAL, P->yN);
             kn_resid<<<g0, NTB, 0, s>>>(S, N0.ne, N0.inc_ptr.as<int32_t>(), N0.inc_src.as<int32_t>(), P->yN, P->at,
@@ -881,6 +910,12 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
     MG_CUDA(cudaMemcpyAsync(&bad, c->flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaStreamSynchronize(s));
     if (bad) mg_fail(MG_ENEWTON, "Newton Jacobian lost positive definiteness (non-finite iterate)");
+    if (mg_trace_level() >= 2) {
+        const double ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        std::fprintf(stderr, "[newton] mesh %d  k %d  iterations %d  rounds %d  column-iterations %d  %.1f ms\n",
+                     op.mesh, io.k, newton_its, rounds, P->flags_h[2], ms);
+    }
     if (counters) {
         counters->step_solves += io.k;
         counters->batched_steps += 1;

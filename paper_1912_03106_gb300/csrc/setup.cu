@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -44,6 +45,14 @@ void DBuf::ensure(size_t nbytes) {
     if (nbytes == 0) nbytes = 16;
     MG_CUDA(cudaMalloc(&p, nbytes));
     bytes = nbytes;
+}
+
+int mg_trace_level() {
+    static const int level = [] {
+        const char* v = std::getenv("MGRIT_EM_TRACE");
+        return v ? std::atoi(v) : 0;
+    }();
+    return level;
 }
 
 void ctx_drop_plans(mg_ctx* c) {

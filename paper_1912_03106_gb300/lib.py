@@ -48,6 +48,7 @@ class mg_solver_opts(C.Structure):
         ("newton_tol", C.c_double),
         ("max_newton", C.c_int),
         ("max_halvings", C.c_int),
+        ("newton_lin_tol", C.c_double),
     ]
 
 
