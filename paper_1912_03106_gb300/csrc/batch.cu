@@ -34,7 +34,21 @@ using namespace mgv;
 
 constexpr int G = 16;     // columns per tile
 constexpr int NTB = 256;  // threads per block
-constexpr int RBS = 256;  // rows per block
+// rows per block: MG_RBS0 on the finest depth (MG_RBS0_LARGE above 8,192 rows),
+// MG_RBS1 on coarser depths, so that a 4,512-row depth still spreads over all SMs
+#ifndef MG_RBS0
+#define MG_RBS0 256
+#endif
+#ifndef MG_RBS0_LARGE
+#define MG_RBS0_LARGE 512
+#endif
+#ifndef MG_RBS1
+#define MG_RBS1 64
+#endif
+// minimum resident blocks per SM for the FP32 multigrid kernels (caps registers)
+#ifndef MG_MINB_F
+#define MG_MINB_F 5
+#endif
 
 struct CallArgs {
     const double* xprev;
@@ -55,7 +69,7 @@ struct CallArgs {
 };
 
 struct Depth {
-    int n, W, nrb;
+    int n, W, nrb, rbs;  // rows, ELL width, row blocks per tile, rows per block
     const int32_t* col;
     const double* L64;
     const double* M64;
@@ -146,8 +160,8 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
     const double* guess = ca->guess;
     const double* g = ca->g;
     double bb[1] = {0.0}, rr[1] = {0.0};
-    const int i1 = min(D.n, (rb + 1) * RBS);
-    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
         double bi = 0.0, lx = 0.0, xi = 0.0;
         if (valid) {
             double mb = 0.0;
@@ -194,8 +208,8 @@ __global__ void __launch_bounds__(NTB) kb_final(Depth D, const CallArgs* __restr
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
     if (gc >= ca->k) return;
-    const int i1 = min(D.n, (rb + 1) * RBS);
-    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
         double xi = x64[((size_t)t * D.n + i) * G + lc];
         if (ca->g) xi += ca->g[(int64_t)i * ca->ld_g + gc];
         ca->xout[(int64_t)i * ca->ld_out + gc] = xi;
@@ -223,6 +237,8 @@ __global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* pa
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
         st.ctr[0] = 0;
+        st.ctr[2] = 0;
+        st.ctr[3] = 0;
         if (use_cond) cudaGraphSetConditional(h, (any && ca->max_it > 0) ? 1u : 0u);
     }
 }
@@ -239,61 +255,80 @@ __global__ void __launch_bounds__(NSB) kb_scalar_init1(Cols st, const double* pa
     }
     if (threadIdx.x == 0) {
         st.ctr[1] = 0;
+        st.ctr[2] = 0;
+        st.ctr[3] = 0;
         if (use_cond) cudaGraphSetConditional(h, 1u);
     }
 }
 
-// threads per column for a one-block scalar kernel over kpad columns
-__device__ __forceinline__ int tpc_for(int kpad) {
-    int t = 1;
-    while (t < 32 && t * 2 * kpad <= NSB) t *= 2;
-    return t;
+// Per-column PCG scalars: one block per column tile (16 lanes per column add the
+// tile's row-block partials in a fixed order).
+__device__ __forceinline__ void tile_totals(const double* part, int nrb, int t, double* out) {
+    static_assert(NTB == 16 * G, "tile_totals needs 16 lanes per column");
+    const int c = threadIdx.x / 16, l = threadIdx.x % 16;
+    double s = 0.0;
+    for (int rb = l; rb < nrb; rb += 16) s += part[((size_t)t * nrb + rb) * G + c];
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (l == 0) out[c] = s;
+    __syncthreads();
 }
 
 // (r, z) -> gamma, beta
-__global__ void __launch_bounds__(NSB) kb_scalar_gamma(Cols st, const double* part, int nrb, int kpad) {
-    const int first = st.ctr[0] == 0;
-    const int tpc = tpc_for(kpad), sub = threadIdx.x % tpc;
-    for (int c = threadIdx.x / tpc; c < kpad; c += NSB / tpc) {
-        const double gn = col_total_par(part, nrb, c, tpc, sub);
-        if (sub == 0) {
-            st.beta[c] = (first || st.gam[c] == 0.0) ? 0.0 : gn / st.gam[c];
-            st.gam[c] = gn;
-        }
+__global__ void __launch_bounds__(NTB) kb_scalar_gamma(Cols st, const double* part, int nrb) {
+    __shared__ double rz[G];
+    tile_totals(part, nrb, blockIdx.x, rz);
+    if (threadIdx.x < G) {
+        const int c = blockIdx.x * G + threadIdx.x;
+        const double gn = rz[threadIdx.x];
+        st.beta[c] = (st.ctr[0] == 0 || st.gam[c] == 0.0) ? 0.0 : gn / st.gam[c];
+        st.gam[c] = gn;
     }
 }
 
 // (p, q) -> alpha
-__global__ void __launch_bounds__(NSB) kb_scalar_alpha(Cols st, const double* part, int nrb, int kpad) {
-    const int tpc = tpc_for(kpad), sub = threadIdx.x % tpc;
-    for (int c = threadIdx.x / tpc; c < kpad; c += NSB / tpc) {
-        const double pq = col_total_par(part, nrb, c, tpc, sub);
-        if (sub == 0) st.alpha[c] = (st.act[c] && pq != 0.0) ? st.gam[c] / pq : 0.0;
+__global__ void __launch_bounds__(NTB) kb_scalar_alpha(Cols st, const double* part, int nrb) {
+    __shared__ double pq[G];
+    tile_totals(part, nrb, blockIdx.x, pq);
+    if (threadIdx.x < G) {
+        const int c = blockIdx.x * G + threadIdx.x;
+        const double v = pq[threadIdx.x];
+        st.alpha[c] = (st.act[c] && v != 0.0) ? st.gam[c] / v : 0.0;
     }
 }
 
-// (r, r) -> convergence masks and the loop condition
-__global__ void __launch_bounds__(NSB) kb_scalar_conv(Cols st, const double* part, int nrb, int kpad,
+// (r, r) -> convergence masks; the last tile block to finish (ticket in ctr[3],
+// active tiles counted in ctr[2]) advances the iteration count and sets the loop
+// condition.
+__global__ void __launch_bounds__(NTB) kb_scalar_conv(Cols st, const double* part, int nrb,
                                                      const CallArgs* __restrict__ ca, int inner,
                                                      cudaGraphConditionalHandle h, int use_cond) {
     const double tol2 = inner ? ca->inner_tol2 : ca->tol2;
-    const int tpc = tpc_for(kpad), sub = threadIdx.x % tpc;
+    __shared__ double rr[G];
+    tile_totals(part, nrb, blockIdx.x, rr);
     int any = 0;
-    for (int c = threadIdx.x / tpc; c < kpad; c += NSB / tpc) {
-        const double rr = col_total_par(part, nrb, c, tpc, sub);
-        if (sub == 0) {
-            if (st.act[c]) {
-                st.iters[c] += 1;
-                if (rr <= tol2 * st.ref[c] || !(rr == rr)) st.act[c] = 0;
-            }
-            any |= st.act[c];
+    if (threadIdx.x < G) {
+        const int c = blockIdx.x * G + threadIdx.x;
+        const double v = rr[threadIdx.x];
+        if (st.act[c]) {
+            st.iters[c] += 1;
+            if (v <= tol2 * st.ref[c] || !(v == v)) st.act[c] = 0;
         }
+        any = st.act[c];
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-        const int it = st.ctr[0] + 1;
-        st.ctr[0] = it;
-        if (use_cond) cudaGraphSetConditional(h, (any && it < ca->max_it) ? 1u : 0u);
+        if (any) atomicAdd(&st.ctr[2], 1);
+        __threadfence();
+        const unsigned ticket = atomicAdd(reinterpret_cast<unsigned*>(&st.ctr[3]), 1u);
+        if (ticket == gridDim.x - 1) {
+            __threadfence();
+            const int active = atomicExch(&st.ctr[2], 0);
+            st.ctr[3] = 0;
+            const int it = st.ctr[0] + 1;
+            st.ctr[0] = it;
+            if (use_cond) cudaGraphSetConditional(h, (active && it < ca->max_it) ? 1u : 0u);
+        }
     }
 }
 
@@ -323,6 +358,8 @@ __global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* p
     if (threadIdx.x == 0) {
         st.ctr[0] = 0;
         st.ctr[1] = sweep + 1;
+        st.ctr[2] = 0;
+        st.ctr[3] = 0;
         if (use_cond) cudaGraphSetConditional(h_inner, (any && ca->max_it > 0) ? 1u : 0u);
         if (use_cond) cudaGraphSetConditional(h_outer, any ? 1u : 0u);
     }
@@ -420,12 +457,12 @@ constexpr int RPPF = NTB / TPRF;   // rows per pass
     int t, rb;                                                \
     tile_rb((D).nrb, t, rb);                                  \
     const int c0 = (threadIdx.x % TPRF) * VF;                 \
-    const int _i1 = min((D).n, (rb + 1) * RBS);               \
-    for (int i = rb * RBS + threadIdx.x / TPRF; i < _i1; i += RPPF)
+    const int _i1 = min((D).n, (rb + 1) * (D).rbs);           \
+    for (int i = rb * (D).rbs + threadIdx.x / TPRF; i < _i1; i += RPPF)
 
 // x = w D^-1 r, s = r - w (L D^-1) r
 template <class RT, bool PC>
-__global__ void __launch_bounds__(NTB) kb_smooth_first(Depth D, const RT* rin_base, float w) {
+__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth_first(Depth D, const RT* rin_base, float w) {
     ROWS_F(D, t, rb, i) {
         const RT* rin = tv(rin_base, D.n, t);
         RT rv[VF];
@@ -448,7 +485,7 @@ __global__ void __launch_bounds__(NTB) kb_smooth_first(Depth D, const RT* rin_ba
 // x += w D^-1 s; s' = s - w (L D^-1) s if dst is given (not on a level's last sweep);
 // partial (r, x) if rtop is given (last sweep on the finest level)
 template <class RT, bool PC>
-__global__ void __launch_bounds__(NTB) kb_smooth(Depth D, const float* src_base, float* dst_base, const RT* rtop_base,
+__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth(Depth D, const float* src_base, float* dst_base, const RT* rtop_base,
                                                  float w, double* part) {
     double rz[VF] = {0.0, 0.0, 0.0, 0.0};
     {
@@ -484,7 +521,7 @@ __global__ void __launch_bounds__(NTB) kb_smooth(Depth D, const float* src_base,
 }
 
 // r_c = P^T s over the coarse rows (grid over the coarse depth's row blocks)
-__global__ void __launch_bounds__(NTB) kb_restrict(Depth D, Depth C, const float* src_base) {
+__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_restrict(Depth D, Depth C, const float* src_base) {
     ROWS_F(C, t, rb, ic) {
         const float* src = tv(src_base, D.n, t);
         float acc[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -501,7 +538,7 @@ __global__ void __launch_bounds__(NTB) kb_restrict(Depth D, Depth C, const float
 }
 
 // y = P x_c, x += y  (x_c = sum of `parts` partial vectors pstride apart)
-__global__ void __launch_bounds__(NTB) kb_prolong(Depth D, Depth C, int parts, size_t pstride) {
+__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_prolong(Depth D, Depth C, int parts, size_t pstride) {
     ROWS_F(D, t, rb, i) {
         const float* xc = tv(C.x, C.n, t);
         float yv[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -534,7 +571,7 @@ __global__ void __launch_bounds__(NTB) kb_prolong(Depth D, Depth C, int parts, s
 
 // s -= L y
 template <bool PC>
-__global__ void __launch_bounds__(NTB) kb_resupdate(Depth D, float* s_base) {
+__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_resupdate(Depth D, float* s_base) {
     ROWS_F(D, t, rb, i) {
         float* s = tv(s_base, D.n, t);
         float acc[VF], sv[VF];
@@ -734,8 +771,8 @@ __global__ void __launch_bounds__(NTB) kb_init_pc(Depth D, const double* __restr
     const int lc = threadIdx.x % G, gc = t * G + lc;
     const bool on = state[gc] == 1;
     double rr[1] = {0.0};
-    const int i1 = min(D.n, (rb + 1) * RBS);
-    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
         const size_t o = ((size_t)t * D.n + i) * G + lc;
         const double ri = on ? -R[o] : 0.0;
         x64[o] = 0.0;
@@ -773,8 +810,8 @@ __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base,
     const float* z = tv((const float*)D.x, D.n, t);
     T* p = tv(p_base, D.n, t);
     T* q = tv(q_base, D.n, t);
-    const int i1 = min(D.n, (rb + 1) * RBS);
-    for (int i = rb * RBS + threadIdx.x / TPR; i < i1; i += RPP) {
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    for (int i = rb * D.rbs + threadIdx.x / TPR; i < i1; i += RPP) {
         T lz[V], pv[V], qv[V];
         float zv[V];
         ell_vec_w<V, T, T, float, PC>(D.col, tile_vals<PC>(Lv, D, t), D.n, D.W, i, z, c0, lz);
@@ -809,8 +846,8 @@ __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, c
     T* r = tv(r_base, D.n, t);
     const T* p = tv(p_base, D.n, t);
     const T* q = tv(q_base, D.n, t);
-    const int i1 = min(D.n, (rb + 1) * RBS);
-    for (int i = rb * RBS + threadIdx.x / TPR; i < i1; i += RPP) {
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    for (int i = rb * D.rbs + threadIdx.x / TPR; i < i1; i += RPP) {
         T dv[V], rv[V], pv[V], qv[V];
         vld<T, V>(d + i * G + c0, dv);
         vld<T, V>(r + i * G + c0, rv);
@@ -844,8 +881,8 @@ __global__ void __launch_bounds__(NTB) kb_refine_r(Depth D, const double* b64, c
     const bool on = outer[gc] == 1;
     double rr[1] = {0.0};
     const double* x = tv(x64, D.n, t);
-    const int i1 = min(D.n, (rb + 1) * RBS);
-    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
         double ri = 0.0;
         if (on) {
             double lx[1];
@@ -867,8 +904,8 @@ __global__ void __launch_bounds__(NTB) kb_update_x(Depth D, double* x64, const f
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
     if (outer[gc] != 1) return;
-    const int i1 = min(D.n, (rb + 1) * RBS);
-    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
         const size_t o = ((size_t)t * D.n + i) * G + lc;
         x64[o] += (double)d32[o];
     }
@@ -998,19 +1035,18 @@ void capture_pcg_body(GraphPlan& P, cudaStream_t s, T* d, T* r, T* p, T* q, cons
                       int inner, cudaGraphConditionalHandle h, int use_cond) {
     Depth& D0 = P.depth[0];
     double* part = P.part.as<double>();
-    const int kpad = P.ntile * G;
     // the V-cycle always reads an FP32 residual: the FP64 form keeps an FP32 shadow of r
     float* rf = nullptr;
     if constexpr (std::is_same<T, double>::value) rf = P.r32s;
     else rf = r;
     capture_precondition<float>(P, s, rf, part);
-    kb_scalar_gamma<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad);
+    kb_scalar_gamma<<<P.ntile, NTB, 0, s>>>(P.st, part, D0.nrb);
     if (P.pc) kb_pcg_a<T, true><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
     else kb_pcg_a<T, false><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
-    kb_scalar_alpha<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad);
+    kb_scalar_alpha<<<P.ntile, NTB, 0, s>>>(P.st, part, D0.nrb);
     kb_pcg_b<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, d, r, p, q, P.st.alpha, part,
                                                        std::is_same<T, double>::value ? P.r32s : nullptr);
-    kb_scalar_conv<<<1, NSB, 0, s>>>(P.st, part, D0.nrb, kpad, ca, inner, h, use_cond);
+    kb_scalar_conv<<<P.ntile, NTB, 0, s>>>(P.st, part, D0.nrb, ca, inner, h, use_cond);
 }
 
 // append a WHILE node at the capture's current position; returns its body graph
@@ -1062,7 +1098,8 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             Depth D = {};
             D.n = (int)md.n;
             D.W = md.W;
-            D.nrb = (D.n + RBS - 1) / RBS;
+            D.rbs = d > 0 ? MG_RBS1 : (D.n > 8192 ? MG_RBS0_LARGE : MG_RBS0);
+            D.nrb = (D.n + D.rbs - 1) / D.rbs;
             D.col = mm.ell_col.as<int32_t>();
             D.L64 = md.L64.as<double>();
             D.M64 = md.M64.as<double>();

@@ -164,16 +164,19 @@ def run_mgrit(ctx, N, T, n, opts):
 
 @pytest.mark.parametrize("relax", [0, 1])
 def test_two_level_cfg0_matches_sequential_oracle(meshes, lin5k, relax):
-    """2-level MGRIT at the 24 x 48 mesh, N = 256, m = 16 (F and FCF)."""
+    """2-level MGRIT at the 24 x 48 mesh, N = 256, m = 16 (F and FCF).  The stop is
+    absolute (1e-11): the GPU's residual has a floor near 2e-13 from the 1e-13
+    step-solve tolerance, above 1e-11 relative to FCF's small first residual."""
     model, ctx, ids = lin5k
     N, T = 256, 5e-3
     P = MachineProblem(meshes, model, N, T, (0, 0), (16,))
     ref = P.sequential()
-    opts = api.mgrit_opts(levels=2, m=(16,), space_level=(ids[0], ids[0]), relax=relax, tol=1e-11)
+    opts = api.mgrit_opts(levels=2, m=(16,), space_level=(ids[0], ids[0]), relax=relax, tol=1e-11,
+                          tol_relative=False)
     got, st = run_mgrit(ctx, N, T, ref.shape[1], opts)
     assert rel_err_per_point(got, ref).max() <= 1e-10
     # iterate parity: the residual history follows the oracle's MGRIT with the same options
-    _, hist = P.mgrit(gamma=relax, tol=1e-11, max_iter=st["iters"])
+    _, hist = P.mgrit(gamma=relax, tol=1e-11, max_iter=st["iters"], tol_relative=False)
     k = min(len(hist), len(st["res_hist"]), 6)
     h_gpu, h_cpu = np.array(st["res_hist"][:k]), np.array(hist[:k])
     assert np.all(np.abs(h_gpu - h_cpu) <= 1e-6 * h_cpu + 1e-9 * h_cpu[0]), (h_gpu, h_cpu)
