@@ -88,23 +88,26 @@ def parse():
     ap.add_argument("--precision", type=int, default=0, help="with --profile-step: 0 FP64, 1 FP32+refinement")
     ap.add_argument("--path", type=int, default=0, help="with --profile-step: 0 auto, 1 cluster, 2 graph")
     ap.add_argument("--reps", type=int, default=2, help="with --profile-step: number of steps")
+    ap.add_argument("--level", type=int, default=2, help="with --profile-step: mesh level 0..3 (18,240 DOFs = 2)")
     return ap.parse_args()
 
 
-def step_inputs(ctx, ids, k):
-    """Seeded start states for batched steps of k columns on the 18,240-DOF mesh:
-    the launch the roofline times and the one the DRAM counters were taken on."""
+def step_inputs(ctx, ids, k, level=2):
+    """Seeded start states for batched steps of k columns on a mesh level (the
+    18,240-DOF level 2 by default): the launch the roofline times and the one the
+    DRAM counters were taken on."""
     import torch
 
-    n = ctx.mg_num_dofs(ids[2])
+    n = ctx.mg_num_dofs(ids[level])
     gen = torch.Generator(device="cuda").manual_seed(0)
     x_in = 0.01 * torch.randn((n, k), dtype=torch.float64, device="cuda", generator=gen)
     return x_in, torch.zeros((n, k), dtype=torch.float64, device="cuda")
 
 
 def profile_step(args):
-    """Batched backward-Euler steps of K columns (18,240 DOFs), nothing else: a short,
-    fixed program for kernel profilers.  Iteration limits count as success."""
+    """Batched backward-Euler steps of K columns on one mesh level, nothing else: a
+    short, fixed program for kernel profilers (one untimed step, then --reps steps
+    timed with CUDA events).  Iteration limits count as success."""
     import torch
 
     import synth
@@ -112,14 +115,35 @@ def profile_step(args):
     from paper_1912_03106_gb300 import api
 
     ctx = api.Context(0)
-    ids = api.setup_machine(ctx, synth.mesh_hierarchy(3), machine_model(pwm=PwmSpec(J0=1e6, f_carrier=F_CARRIER)))
-    x_in, out = step_inputs(ctx, ids, args.profile_step)
+    ids = api.setup_machine(ctx, synth.mesh_hierarchy(max(3, args.level + 1)),
+                            machine_model(pwm=PwmSpec(J0=1e6, f_carrier=F_CARRIER)))
+    k = args.profile_step
+    x_in, out = step_inputs(ctx, ids, k, args.level)
     so = api.solver_opts(precision=args.precision, path=args.path)
-    for _ in range(args.reps):
-        _, st = ctx.mg_step(ids[2], N_STEPS, T_END, x_in, out, i0=1, istride=1 if x_in.shape[1] > 1 else 0,
-                            solver=so, allow=(-5,))
+
+    def step():
+        return ctx.mg_step(ids[args.level], N_STEPS, T_END, x_in, out, i0=1, istride=1 if k > 1 else 0,
+                           solver=so, allow=(-5,))[1]
+
+    st = step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_step": args.profile_step, "pcg_iters": st["cg_iters"]}))
+    e0.record(ctx.stream)
+    iters = 0
+    for _ in range(args.reps):
+        st = step()
+        iters += st["cg_iters"]
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.reps)
+    it_col = iters / max(1, args.reps) / k
+    ns = [ctx.mg_num_dofs(ids[lv]) for lv in range(args.level, -1, -1)]  # multigrid depths
+    kb = 8 if args.precision == 0 else 4
+    per_col = step_bytes_per_column_iteration(ns, krylov_bytes=kb)
+    alg = it_col * (k * per_col + matrix_bytes_per_iteration(ns)) + k * ns[0] * 8 * 9
+    print(json.dumps({"profile_step": k, "level": args.level, "dofs": ns[0], "precision": args.precision,
+                      "ms": ms, "pcg_iters_per_column": it_col, "algorithmic_bytes": alg,
+                      "algorithmic_gbs": alg / ms / 1e6}))
 
 
 def dist_info():

@@ -608,42 +608,43 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-constexpr int BK = 128;         // K chunk staged in shared memory
 constexpr int BASE_KSPLIT = 4;  // K splits of the dense base solve (partials summed by the prolongation)
 
-// The K range is split over `ks` blocks per output tile (grid = row blocks x tiles
-// x ks); split s writes its partial product to x_base + s * pstride, and the
-// consumer adds the ks partials in order.
-template <class RT>
+// A block computes 64 rows x TB column tiles (TB x 16 columns) over one K range,
+// staging BKT columns of A's 64-row slice and BKT rows of r per step, so one A
+// slice serves TB tiles.  The K range is split over `ks` blocks per output block
+// (grid = ks x row blocks x column groups, split fastest); split s writes its
+// partial product to x_base + s * pstride and the consumer adds the ks partials
+// in order.
+template <class RT, int TB, int BKT>
 __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __restrict__ A, const RT* r_base,
                                                      float* x_base, int ntile, int ks, size_t pstride) {
-    __shared__ __align__(16) float As[64][BK + 4];  // +4: conflict-free fragment reads
-    __shared__ float Bs[BK][G + 8];
+    __shared__ __align__(16) float As[64][BKT + 4];    // +4: conflict-free fragment reads
+    __shared__ __align__(16) float Bs[BKT][TB * G + 8];  // +8: conflict-free fragment reads
     const int nrb = (n0 + 63) / 64;
     const int split = blockIdx.x % ks, bt = blockIdx.x / ks;
-    const int t = bt / nrb, ib = bt % nrb;
-    const int kspan = ((n0 + ks - 1) / ks + BK - 1) / BK * BK;
+    const int cg = bt / nrb, ib = bt % nrb;
+    const int kspan = ((n0 + ks - 1) / ks + BKT - 1) / BKT * BKT;
     const int kbeg = split * kspan, kend = min(n0, kbeg + kspan);
     x_base += (size_t)split * pstride;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tig = lane & 3;
-    const RT* rb = r_base + (size_t)t * n0 * G;
-    float acc[2][4] = {};
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        // stage A[ib*64 .. +64][k0 .. k0+BK) and r[k0 .. k0+BK][0 .. 16)
-        for (int q = threadIdx.x; q < 64 * BK; q += 128) {
-            const int rr = q / BK, kk = q % BK;
+    float acc[2 * TB][4] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += BKT) {
+        // stage A[ib*64 .. +64][k0 .. k0+BKT) and r[k0 .. k0+BKT][tiles cg*TB .. +TB)
+        for (int q = threadIdx.x; q < 64 * BKT; q += 128) {
+            const int rr = q / BKT, kk = q % BKT;
             const int gi = ib * 64 + rr, gk = k0 + kk;
             As[rr][kk] = (gi < n0 && gk < kend) ? __ldg(A + (size_t)gi * n0 + gk) : 0.0f;
         }
-        for (int q = threadIdx.x; q < BK * G; q += 128) {
-            const int kk = q / G, cc = q % G;
-            const int gk = k0 + kk;
-            Bs[kk][cc] = gk < kend ? (float)rb[(size_t)gk * G + cc] : 0.0f;
+        for (int q = threadIdx.x; q < BKT * TB * G; q += 128) {
+            const int kk = q / (TB * G), cc = q % (TB * G);
+            const int t = cg * TB + cc / G, gk = k0 + kk;
+            Bs[kk][cc] = (gk < kend && t < ntile) ? (float)r_base[((size_t)t * n0 + gk) * G + cc % G] : 0.0f;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < BK; kk += 8) {
+#pragma unroll 2
+        for (int kk = 0; kk < BKT; kk += 8) {
             const int ra = warp * 16 + g;
             unsigned ahi[4], alo[4];
             split_tf32(As[ra][kk + tig], ahi[0], alo[0]);
@@ -651,7 +652,7 @@ __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __rest
             split_tf32(As[ra][kk + tig + 4], ahi[2], alo[2]);
             split_tf32(As[ra + 8][kk + tig + 4], ahi[3], alo[3]);
 #pragma unroll
-            for (int f = 0; f < 2; ++f) {
+            for (int f = 0; f < 2 * TB; ++f) {
                 unsigned bh0, bl0, bh1, bl1;
                 split_tf32(Bs[kk + tig][f * 8 + g], bh0, bl0);
                 split_tf32(Bs[kk + tig + 4][f * 8 + g], bh1, bl1);
@@ -662,11 +663,13 @@ __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __rest
         }
         __syncthreads();
     }
-    float* xb = x_base + (size_t)t * n0 * G;
     const int ra = ib * 64 + warp * 16 + g, rb8 = ra + 8;
 #pragma unroll
-    for (int f = 0; f < 2; ++f) {
-        const int cc = f * 8 + tig * 2;
+    for (int f = 0; f < 2 * TB; ++f) {
+        const int t = cg * TB + f / 2;
+        if (t >= ntile) continue;
+        float* xb = x_base + (size_t)t * n0 * G;
+        const int cc = (f % 2) * 8 + tig * 2;
         if (ra < n0) {
             xb[(size_t)ra * G + cc] = acc[f][0];
             xb[(size_t)ra * G + cc + 1] = acc[f][1];
@@ -675,6 +678,26 @@ __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __rest
             xb[(size_t)rb8 * G + cc] = acc[f][2];
             xb[(size_t)rb8 * G + cc + 1] = acc[f][3];
         }
+    }
+}
+
+// launch the dense base solve with TB tiles per block for ntile tiles
+#ifndef MG_BASE_TB
+#define MG_BASE_TB 2
+#endif
+template <class RT>
+void launch_base_dense(cudaStream_t s, int n0, const float* A, const RT* r, float* x, int ntile, int ks,
+                       size_t pstride) {
+    const int nrb = (n0 + 63) / 64;
+    if (MG_BASE_TB >= 4 && ks > 1 && ntile >= 4) {
+        const unsigned nb = (unsigned)(nrb * ((ntile + 3) / 4) * ks);
+        kb_base_dense<RT, 4, 64><<<nb, 128, 0, s>>>(n0, A, r, x, ntile, ks, pstride);
+    } else if (MG_BASE_TB >= 2 && ks > 1 && ntile >= 2) {
+        const unsigned nb = (unsigned)(nrb * ((ntile + 1) / 2) * ks);
+        kb_base_dense<RT, 2, 64><<<nb, 128, 0, s>>>(n0, A, r, x, ntile, ks, pstride);
+    } else {
+        const unsigned nb = (unsigned)(nrb * ntile * ks);
+        kb_base_dense<RT, 1, 128><<<nb, 128, 0, s>>>(n0, A, r, x, ntile, ks, pstride);
     }
 }
 
@@ -981,7 +1004,6 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
     Depth& B = P.depth[nd - 1];
     const size_t pstride = (size_t)P.ntile * B.n * G;
     const int ks = nd == 1 ? 1 : BASE_KSPLIT;
-    const int nbg = ((B.n + 63) / 64) * P.ntile * ks;
     int parts = 1;
     if (PC) {
         const unsigned nb = (unsigned)(P.ntile * G / BAND_WARPS);
@@ -991,9 +1013,8 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
         else kb_base_band<float><<<nb, 32 * BAND_WARPS, smem, s>>>(B.n, P.pco.band_u, P.pco.band_stride,
                                                                   P.pco.band_L, P.pco.band_U, B.r, B.x);
     } else if (P.op->base_inv.p) {
-        if (nd == 1) kb_base_dense<RT><<<nbg, 128, 0, s>>>(B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0);
-        else kb_base_dense<float><<<nbg, 128, 0, s>>>(B.n, P.op->base_inv.as<float>(), B.r, B.x, P.ntile, ks,
-                                                      pstride);
+        if (nd == 1) launch_base_dense<RT>(s, B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0);
+        else launch_base_dense<float>(s, B.n, P.op->base_inv.as<float>(), B.r, B.x, P.ntile, ks, pstride);
         parts = ks;
     } else {
         if (nd == 1) kb_jacobi<RT, PC><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, rtop, w, nullptr);
