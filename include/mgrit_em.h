@@ -156,6 +156,11 @@ typedef struct {
     double newton_lin_tol; /* PCG stop of each correction: ||J delta + F|| <= newton_lin_tol ||F||
                               (an inexact Newton step; the last correction is below newton_tol,
                               so its relative error does not reach the result)               */
+    /* launch shape of the graph path; 0 = library choice, or the shape mg_autotune
+     * recorded in the context for this mesh and column count */
+    int rows_per_block;        /* rows per block on the finest multigrid depth (16..4096)   */
+    int coarse_rows_per_block; /* rows per block on the coarser depths (16..4096)           */
+    int base_tiles;            /* 16-column tiles per block of the dense base solve (1, 2, 4) */
 } mg_solver_opts;
 
 /* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,
@@ -219,6 +224,22 @@ mg_status mg_step_static(mg_ctx* ctx, int level, int64_t N, double T, int64_t dt
                          double* x_out, int64_t ld_out, int guess, const mg_solver_opts* opts,
                          mg_stats* stats);
 
+/* Autotuner (the paper has no counterpart): times batched linear steps of k
+ * columns on mesh `level` (dt = T/N; start states are a fixed pseudo-random
+ * pattern generated on the device) for a set of launch shapes -- cluster path
+ * with tile width 1/8/16 and 8 or 16 CTAs per cluster, or graph path with rows
+ * per block on the finest and coarser depths and base-solve tiles per block --
+ * by coordinate descent from the library's choice, 3 timed steps per shape.
+ * The fastest shape is written into *opts (path, tile, cluster, rows_per_block,
+ * coarse_rows_per_block, base_tiles; other fields kept) and recorded in the
+ * context for (level, k) -- k rounded up to whole 16-column tiles above 16 --,
+ * where steps with path MG_PATH_AUTO and a zero shape pick it up (MGRIT
+ * relaxation batches included).  best_ms (may
+ * be NULL) receives the time per step of the chosen shape.  Allocates device
+ * memory for the trial vectors; synchronises.  Nonlinear meshes: MG_EINVAL. */
+mg_status mg_autotune(mg_ctx* ctx, int level, int64_t N, double T, int k, mg_solver_opts* opts,
+                      double* best_ms);
+
 /* Sequential time stepping (forward block solve, Sec. 2): out[0] = a0,
  * out[i] = Phi_i(out[i-1]), i = 1..N, on mesh `level` with dt = T/N.
  * a0: n doubles; out: (N+1)*n doubles, time-major (device pointers). */
@@ -249,6 +270,20 @@ void mg_opts_defaults(mg_opts* opts);
  * the tolerance was not reached (out holds the last iterate). */
 mg_status mg_solve(mg_ctx* ctx, int64_t N, double T, const double* a0, double* out,
                    const mg_opts* opts, mg_stats* stats);
+
+/* Several independent machine instances at once (the paper has no counterpart):
+ * instance i is context ctxs[i] (its own meshes, materials, PWM and stream; the
+ * contexts must be distinct and should use distinct streams) solved with N[i],
+ * T[i], a0[i], out[i] (device pointers, layouts as mg_solve) by mg_solve with
+ * opts[i], or by mg_sequential on opts[i].space_level[0] with opts[i].solver when
+ * opts[i].levels == 1.  Each instance is driven by a host worker thread, at most
+ * max_threads at a time (0 = one per instance), so the instances' kernels run
+ * concurrently on the GPU.  status[i] and stats[i] (either may be NULL) receive
+ * each instance's status and statistics; the call returns the worst status and
+ * returns when every instance's stream is idle. */
+mg_status mg_batch_solve(mg_ctx* const* ctxs, int n, const int64_t* N, const double* T,
+                         const double* const* a0, double* const* out, const mg_opts* opts,
+                         int max_threads, mg_status* status, mg_stats* stats);
 
 /* As mg_solve / mg_sequential with HOST a0 and out: the call copies a0 to the
  * device, solves, and copies the trajectory back (both copies on the stream). */

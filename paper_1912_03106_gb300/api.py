@@ -190,6 +190,14 @@ class Context:
         self._check(rc, allow=allow)
         return rc, stats_dict(st)
 
+    def mg_autotune(self, level, N, T, k, solver=None):
+        """Returns (tuned solver options, ms per step of the chosen launch shape)."""
+        so = solver or solver_opts()
+        ms = C.c_double(0.0)
+        rc = self.lib.mg_autotune(self.h, level, N, T, k, C.byref(so), C.byref(ms))
+        self._check(rc)
+        return so, ms.value
+
     def mg_sequential(self, level, N, T, a0, out, solver=None, allow=()):
         _dev64(a0, "a0")
         _dev64(out, "out")
@@ -240,3 +248,26 @@ def setup_machine(ctx: Context, meshes, model) -> list:
     p = model.pwm
     ctx.mg_set_pwm(p.J0, p.f_ref, p.f_carrier, p.carrier, p.mod_index)
     return ids
+
+
+def mg_batch_solve(ctxs, N, T, a0, out, opts, max_threads=0):
+    """Solve independent instances concurrently (one Context each, distinct streams).
+
+    N, T, a0, out, opts: one entry per instance (a0/out device tensors as for
+    Context.mg_solve).  Returns (worst status, [status], [stats dict]).
+    """
+    n = len(ctxs)
+    lib = L.load()
+    for a, o in zip(a0, out):
+        _dev64(a, "a0")
+        _dev64(o, "out")
+    hs = (C.c_void_p * n)(*[c.h.value if isinstance(c.h, C.c_void_p) else c.h for c in ctxs])
+    Ns = (C.c_int64 * n)(*N)
+    Ts = (C.c_double * n)(*T)
+    a0p = (C.c_void_p * n)(*[a.data_ptr() for a in a0])
+    outp = (C.c_void_p * n)(*[o.data_ptr() for o in out])
+    op = (L.mg_opts * n)(*opts)
+    st = (C.c_int * n)()
+    stats = (L.mg_stats * n)()
+    rc = lib.mg_batch_solve(hs, n, Ns, Ts, a0p, outp, op, max_threads, st, stats)
+    return rc, [L.STATUS.get(v, v) for v in st], [stats_dict(s) for s in stats]

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgrit_em.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cu", "pcg.cu", "batch.cu", "newton.cu", "mgrit.cu"]
+SOURCES = ["setup.cu", "pcg.cu", "batch.cu", "newton.cu", "mgrit.cu", "tune.cu", "instances.cu"]
 
 
 def nvcc() -> str:

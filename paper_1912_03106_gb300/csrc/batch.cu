@@ -687,12 +687,13 @@ __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __rest
 #endif
 template <class RT>
 void launch_base_dense(cudaStream_t s, int n0, const float* A, const RT* r, float* x, int ntile, int ks,
-                       size_t pstride) {
+                       size_t pstride, int tb) {
     const int nrb = (n0 + 63) / 64;
-    if (MG_BASE_TB >= 4 && ks > 1 && ntile >= 4) {
+    if (tb <= 0) tb = ks > 1 ? MG_BASE_TB : 1;  // library choice
+    if (tb >= 4 && ntile >= 4) {
         const unsigned nb = (unsigned)(nrb * ((ntile + 3) / 4) * ks);
         kb_base_dense<RT, 4, 64><<<nb, 128, 0, s>>>(n0, A, r, x, ntile, ks, pstride);
-    } else if (MG_BASE_TB >= 2 && ks > 1 && ntile >= 2) {
+    } else if (tb >= 2 && ntile >= 2) {
         const unsigned nb = (unsigned)(nrb * ((ntile + 1) / 2) * ks);
         kb_base_dense<RT, 2, 64><<<nb, 128, 0, s>>>(n0, A, r, x, ntile, ks, pstride);
     } else {
@@ -941,6 +942,7 @@ struct GraphPlan {
     const StepOp* op = nullptr;
     int ntile = 0, precision = 0, precond = 1, nu = 2;
     bool pc = false;   // per-column operators (Newton Jacobians), see graph_plan_pc
+    int rbs0 = 0, rbs1 = 0, base_tb = 0;  // launch shape (0: library choice)
     PcOperator pco{};
     float omega = 0.7f;
     std::vector<DBuf> bufs;
@@ -1013,8 +1015,9 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
         else kb_base_band<float><<<nb, 32 * BAND_WARPS, smem, s>>>(B.n, P.pco.band_u, P.pco.band_stride,
                                                                   P.pco.band_L, P.pco.band_U, B.r, B.x);
     } else if (P.op->base_inv.p) {
-        if (nd == 1) launch_base_dense<RT>(s, B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0);
-        else launch_base_dense<float>(s, B.n, P.op->base_inv.as<float>(), B.r, B.x, P.ntile, ks, pstride);
+        if (nd == 1) launch_base_dense<RT>(s, B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0, P.base_tb);
+        else launch_base_dense<float>(s, B.n, P.op->base_inv.as<float>(), B.r, B.x, P.ntile, ks, pstride,
+                                      P.base_tb);
         parts = ks;
     } else {
         if (nd == 1) kb_jacobi<RT, PC><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, rtop, w, nullptr);
@@ -1103,6 +1106,9 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
     try {
         P->op = &op;
         P->ntile = ntile;
+        P->rbs0 = so.rows_per_block;
+        P->rbs1 = so.coarse_rows_per_block;
+        P->base_tb = so.base_tiles;
         if (pco) {
             P->pc = true;
             P->pco = *pco;
@@ -1119,7 +1125,8 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             Depth D = {};
             D.n = (int)md.n;
             D.W = md.W;
-            D.rbs = d > 0 ? MG_RBS1 : (D.n > 8192 ? MG_RBS0_LARGE : MG_RBS0);
+            if (d > 0) D.rbs = so.coarse_rows_per_block > 0 ? so.coarse_rows_per_block : MG_RBS1;
+            else D.rbs = so.rows_per_block > 0 ? so.rows_per_block : (D.n > 8192 ? MG_RBS0_LARGE : MG_RBS0);
             D.nrb = (D.n + D.rbs - 1) / D.rbs;
             D.col = mm.ell_col.as<int32_t>();
             D.L64 = md.L64.as<double>();
@@ -1283,7 +1290,8 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
     GraphPlan* P = nullptr;
     for (auto* q : c->plans)
         if (!q->pc && q->op == &op && q->ntile == ntile && q->precision == so.precision && q->precond == so.precond &&
-            q->nu == (so.smooth > 0 ? so.smooth : 2) && q->omega == (so.omega > 0.0 ? (float)so.omega : 0.7f)) {
+            q->nu == (so.smooth > 0 ? so.smooth : 2) && q->omega == (so.omega > 0.0 ? (float)so.omega : 0.7f) &&
+            q->rbs0 == so.rows_per_block && q->rbs1 == so.coarse_rows_per_block && q->base_tb == so.base_tiles) {
             P = q;
             break;
         }

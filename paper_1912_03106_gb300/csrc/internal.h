@@ -159,6 +159,11 @@ struct mg_ctx {
     std::vector<GraphPlan*> plans;  // graph-path step plans (buffers + instantiated graphs)
     std::vector<NewtonPlan*> nplans;  // Newton-step plans (own their per-column PCG graphs)
     std::map<int, NlMesh*> nl;       // mesh -> static data of its nonlinear elements
+    struct Shape {                   // launch shape chosen by mg_autotune
+        int path, tile, cluster, rbs0, rbs1, base_tiles;
+        double ms;
+    };
+    std::map<std::pair<int, int>, Shape> tuned;  // (mesh, column bucket) -> shape
     ~mg_ctx();
 };
 
@@ -204,6 +209,8 @@ void ctx_drop_plans(mg_ctx* c);
 // Diagnostics on stderr, from the environment variable MGRIT_EM_TRACE: 0 off,
 // 1 one line per MGRIT iteration, 2 also one line per batched Newton step.
 int mg_trace_level();
+// column bucket of the autotuner's table: k itself up to 16, else whole 16-column tiles
+inline int tune_bucket(int k) { return k <= 16 ? k : (k + 15) / 16 * 16; }
 
 // ---- per-column systems: the graph path's PCG with one operator per column
 // (tile-major storage, 16 columns per tile; see batch.cu)

@@ -310,7 +310,10 @@ void check_solver_opts(const mg_solver_opts& so) {
         !(so.inner_tol >= 0.0) || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) || so.cluster < 0 ||
         so.cluster > 16 || !(so.tile == 0 || so.tile == 1 || so.tile == 8 || so.tile == 16 || so.tile == 32) ||
         (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID) || so.smooth < 0 || so.smooth > 8 ||
-        !(so.omega >= 0.0 && so.omega < 2.0) || so.path < MG_PATH_AUTO || so.path > MG_PATH_GRAPH)
+        !(so.omega >= 0.0 && so.omega < 2.0) || so.path < MG_PATH_AUTO || so.path > MG_PATH_GRAPH ||
+        !(so.rows_per_block == 0 || (so.rows_per_block >= 16 && so.rows_per_block <= 4096)) ||
+        !(so.coarse_rows_per_block == 0 || (so.coarse_rows_per_block >= 16 && so.coarse_rows_per_block <= 4096)) ||
+        !(so.base_tiles == 0 || so.base_tiles == 1 || so.base_tiles == 2 || so.base_tiles == 4))
         mg_fail(MG_EINVAL, "bad solver options");
 }
 

@@ -945,6 +945,22 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
         phi_batch_newton(c, op, io, so, counters);
         return;
     }
+    if (so.path == MG_PATH_AUTO && so.tile == 0 && so.cluster == 0 && so.rows_per_block == 0 &&
+        so.coarse_rows_per_block == 0 && so.base_tiles == 0) {
+        // a launch shape mg_autotune recorded for this mesh and tile count
+        auto it = c->tuned.find({op.mesh, tune_bucket(io.k)});
+        if (it != c->tuned.end()) {
+            mg_solver_opts t = so;
+            t.path = it->second.path;
+            t.tile = it->second.tile;
+            t.cluster = it->second.cluster;
+            t.rows_per_block = it->second.rbs0;
+            t.coarse_rows_per_block = it->second.rbs1;
+            t.base_tiles = it->second.base_tiles;
+            phi_batch(c, op, io, t, counters);
+            return;
+        }
+    }
     if (so.path == MG_PATH_GRAPH || (so.path == MG_PATH_AUTO && io.k >= MG_GRAPH_MIN_COLUMNS)) {
         phi_batch_graph(c, op, io, so, counters);
         return;

@@ -1,0 +1,153 @@
+// Launch-shape autotuner for batched linear steps.
+//
+// The step's work per PCG iteration is fixed by the method; what the hardware
+// makes of it depends on the launch shape: on the cluster path the column tile
+// width and the CTAs per cluster, on the graph path the rows each block owns on
+// the finest and on the coarser multigrid depths (grid size against the 152 SMs)
+// and the column tiles per block of the dense base solve.  mg_autotune times
+// one batched step per candidate shape with CUDA events and keeps the fastest,
+// by coordinate descent from the library's own choice.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+// fixed pseudo-random start states in [-0.01, 0.01] (a counter-based integer hash)
+__global__ void kt_fill(int64_t n, double* x) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint64_t h = (uint64_t)q * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    x[q] = 0.01 * (2.0 * (double)(h >> 11) * (1.0 / 9007199254740992.0) - 1.0);
+}
+
+struct Trial {
+    int path, tile, cluster, rbs0, rbs1, tb;
+};
+
+}  // namespace
+
+extern mg_status mg_guarded_call(mg_ctx* c, void (*fn)(void*), void* arg);
+
+extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int k, mg_solver_opts* opts,
+                                 double* best_ms) {
+    struct Args {
+        mg_ctx* c;
+        int level;
+        int64_t N;
+        double T;
+        int k;
+        mg_solver_opts* opts;
+        double* best_ms;
+    } a{c, level, N, T, k, opts, best_ms};
+    return mg_guarded_call(
+        c,
+        [](void* p) {
+            Args& A = *static_cast<Args*>(p);
+            mg_ctx* c = A.c;
+            if (!A.opts || A.level < 0 || A.level >= (int)c->meshes.size() || A.N <= 0 || !(A.T > 0.0) ||
+                A.k <= 0 || A.k > 65536)
+                mg_fail(MG_EINVAL, "mg_autotune: bad arguments");
+            ctx_finalize(c);
+            if (mesh_is_nonlinear(c, A.level)) mg_fail(MG_EINVAL, "mg_autotune: times linear steps only");
+            const StepOp& op = ctx_step_op(c, A.level, A.T / (double)A.N);
+            const int8_t* signs = ctx_pwm_table(c, A.N, A.T);
+            const int64_t n = c->meshes[A.level].n;
+            DBuf xin, xout;
+            xin.ensure((size_t)n * A.k * sizeof(double));
+            xout.ensure((size_t)n * A.k * sizeof(double));
+            cudaStream_t s = c->stream;
+            kt_fill<<<(unsigned)((n * A.k + 255) / 256), 256, 0, s>>>(n * A.k, xin.as<double>());
+            MG_CUDA(cudaGetLastError());
+            PhiIO io;
+            io.k = A.k;
+            io.xprev = xin.as<double>();
+            io.ld_prev = A.k;
+            io.xout = xout.as<double>();
+            io.ld_out = A.k;
+            io.signs = signs;
+            io.t0 = std::min<int64_t>(1, A.N);
+            io.tstride = A.k > 1 && io.t0 + (int64_t)(A.k - 1) <= A.N ? 1 : 0;
+            cudaEvent_t e0, e1;
+            MG_CUDA(cudaEventCreate(&e0));
+            MG_CUDA(cudaEventCreate(&e1));
+            auto time_of = [&](const Trial& t) {
+                mg_solver_opts so = *A.opts;
+                so.path = t.path;
+                so.tile = t.tile;
+                so.cluster = t.cluster;
+                so.rows_per_block = t.rbs0;
+                so.coarse_rows_per_block = t.rbs1;
+                so.base_tiles = t.tb;
+                phi_batch(c, op, io, so, nullptr);  // builds the plan, warms the caches
+                MG_CUDA(cudaEventRecord(e0, s));
+                for (int r = 0; r < 3; ++r) phi_batch(c, op, io, so, nullptr);
+                MG_CUDA(cudaEventRecord(e1, s));
+                MG_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                return (double)ms / 3.0;
+            };
+            Trial best{};
+            double best_t = std::numeric_limits<double>::infinity();
+            auto consider = [&](const Trial& t) {
+                const double ms = time_of(t);
+                if (ms < best_t) {
+                    best_t = ms;
+                    best = t;
+                }
+            };
+            try {
+                if (A.k < 32) {  // latency-bound: cluster tile width and size, or the graph path
+                    for (int tile : {1, 8, 16})
+                        for (int cl : {8, 16}) consider({MG_PATH_CLUSTER, tile, cl, 0, 0, 0});
+                }
+                Trial gb{MG_PATH_GRAPH, 0, 0, 0, 0, 0};
+                double gt = time_of(gb);
+                for (int r0 : {128, 256, 512, 1024}) {
+                    Trial t = gb;
+                    t.rbs0 = r0;
+                    const double ms = time_of(t);
+                    if (ms < gt) gt = ms, gb = t;
+                }
+                for (int r1 : {32, 64, 128, 256}) {
+                    Trial t = gb;
+                    t.rbs1 = r1;
+                    const double ms = time_of(t);
+                    if (ms < gt) gt = ms, gb = t;
+                }
+                for (int tb : {1, 2, 4}) {
+                    Trial t = gb;
+                    t.tb = tb;
+                    const double ms = time_of(t);
+                    if (ms < gt) gt = ms, gb = t;
+                }
+                if (gt < best_t) best_t = gt, best = gb;
+            } catch (...) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                ctx_drop_plans(c);
+                throw;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            ctx_drop_plans(c);  // the trial plans; the chosen one is rebuilt on first use
+            A.opts->path = best.path;
+            A.opts->tile = best.tile;
+            A.opts->cluster = best.cluster;
+            A.opts->rows_per_block = best.rbs0;
+            A.opts->coarse_rows_per_block = best.rbs1;
+            A.opts->base_tiles = best.tb;
+            c->tuned[{A.level, tune_bucket(A.k)}] = {best.path, best.tile, best.cluster, best.rbs0, best.rbs1, best.tb, best_t};
+            if (A.best_ms) *A.best_ms = best_t;
+        },
+        &a);
+}

@@ -49,6 +49,9 @@ class mg_solver_opts(C.Structure):
         ("max_newton", C.c_int),
         ("max_halvings", C.c_int),
         ("newton_lin_tol", C.c_double),
+        ("rows_per_block", C.c_int),
+        ("coarse_rows_per_block", C.c_int),
+        ("base_tiles", C.c_int),
     ]
 
 
@@ -110,6 +113,10 @@ _SIGNATURES = {
     "mg_solve_host": (C.c_int, [_P, _I64, _D, _P, _P, C.POINTER(mg_opts), C.POINTER(mg_stats)]),
     "mg_sequential_host": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P, C.POINTER(mg_solver_opts),
                                      C.POINTER(mg_stats)]),
+    "mg_autotune": (C.c_int, [_P, C.c_int, _I64, _D, C.c_int, C.POINTER(mg_solver_opts), C.POINTER(_D)]),
+    "mg_batch_solve": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_I64), C.POINTER(_D), C.POINTER(_P),
+                                 C.POINTER(_P), C.POINTER(mg_opts), C.c_int, C.POINTER(C.c_int),
+                                 C.POINTER(mg_stats)]),
 }
 
 EXPORTED = tuple(_SIGNATURES)

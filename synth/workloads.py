@@ -46,3 +46,34 @@ WORKLOADS = {
 
 def workload(name: str) -> Workload:
     return WORKLOADS[name]
+
+
+@dataclasses.dataclass(frozen=True)
+class Instance:
+    """One machine instance of the batching workload (data only)."""
+    mesh_level: int
+    N: int
+    T: float
+    f_carrier: float
+    J0: float
+    nonlinear: bool
+
+
+def instances(count: int = 64, seed: int = 0, mesh_levels=(0, 1, 2, 3), Ns=(1024, 4096, 16384),
+              carriers=(5.0e3, 10.0e3, 20.0e3), J0_range=(0.5e6, 3.0e6), T: float = 20.0e-3,
+              nonlinear_fraction: float = 0.5, nonlinear_levels=None) -> list:
+    """Seeded draw of uneven machine instances (the batching workload: mesh level,
+    N, carrier and J0 drawn uniformly, linear / nonlinear by nonlinear_fraction).
+    nonlinear_levels restricts which mesh levels may carry the nonlinear law."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        lvl = int(rng.choice(mesh_levels))
+        nl = bool(rng.random() < nonlinear_fraction)
+        if nonlinear_levels is not None and lvl not in nonlinear_levels:
+            nl = False
+        out.append(Instance(lvl, int(rng.choice(Ns)), T, float(rng.choice(carriers)),
+                            float(rng.uniform(*J0_range)), nl))
+    return out

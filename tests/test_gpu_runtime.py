@@ -1,0 +1,104 @@
+"""GPU tests of the runtime around the step kernels: the launch-shape autotuner
+and the concurrent solve of many independent machine instances."""
+
+import numpy as np
+import pytest
+
+import synth
+from synth.model import PwmSpec, machine_model
+from synth.workloads import instances
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1912_03106_gb300 import api  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def meshes():
+    return synth.mesh_hierarchy(3)
+
+
+def make_ctx(meshes, model, stream=None):
+    ctx = api.Context(0, stream=stream)
+    ids = api.setup_machine(ctx, meshes, model)
+    return ctx, ids
+
+
+@pytest.mark.parametrize("level,k", [(2, 256), (0, 16), (0, 1)])
+def test_autotune_shape_gives_the_same_step(meshes, level, k):
+    model = machine_model(pwm=PwmSpec(J0=1e6, f_carrier=20e3))
+    ctx, ids = make_ctx(meshes, model)
+    n = ctx.mg_num_dofs(ids[level])
+    x = torch.as_tensor(0.01 * np.random.default_rng(k).standard_normal((n, k)), device="cuda")
+    ref = torch.zeros_like(x)
+    ctx.mg_step(ids[level], 4096, 20e-3, x, ref, i0=1, istride=1 if k > 1 else 0)
+    so, ms = ctx.mg_autotune(ids[level], 4096, 20e-3, k)
+    assert ms > 0.0
+    assert so.path in (1, 2)
+    assert so.base_tiles in (0, 1, 2, 4)
+    got = torch.zeros_like(x)
+    ctx.mg_step(ids[level], 4096, 20e-3, x, got, i0=1, istride=1 if k > 1 else 0, solver=so)
+    err = ((got - ref).norm(dim=0) / ref.norm(dim=0)).max().item()
+    assert err <= 1e-11, err
+    # default options now pick the recorded shape: identical to the explicit run
+    again = torch.zeros_like(x)
+    ctx.mg_step(ids[level], 4096, 20e-3, x, again, i0=1, istride=1 if k > 1 else 0)
+    assert torch.equal(again, got)
+    ctx.close()
+
+
+def test_autotune_rejects_nonlinear_mesh(meshes):
+    ctx, ids = make_ctx(meshes[:1], machine_model(nonlinear=True, pwm=PwmSpec(J0=3e6, f_carrier=20e3)))
+    with pytest.raises(api.L.MgError) as e:
+        ctx.mg_autotune(ids[0], 1024, 5e-3, 16)
+    assert e.value.status == -1
+    ctx.close()
+
+
+def instance_setup(meshes, inst, stream):
+    model = machine_model(nonlinear=inst.nonlinear, pwm=PwmSpec(J0=inst.J0, f_carrier=inst.f_carrier))
+    ctx, ids = make_ctx(meshes[:inst.mesh_level + 1], model, stream=stream)
+    n = ctx.mg_num_dofs(ids[inst.mesh_level])
+    opts = api.mgrit_opts(levels=2, m=(16,), space_level=(ids[inst.mesh_level], ids[inst.mesh_level]), relax=1,
+                          tol=1e-8, max_iter=30)
+    a0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = torch.zeros((inst.N + 1, n), dtype=torch.float64, device="cuda")
+    return ctx, opts, a0, out
+
+
+def test_batch_solve_equals_one_by_one(meshes):
+    """Six uneven instances (meshes l0/l1, N 64/128/256, carriers, J0, one
+    nonlinear) solved concurrently give bit-identical trajectories to solving
+    each alone."""
+    insts = instances(6, seed=3, mesh_levels=(0, 1), Ns=(64, 128, 256), T=2.5e-3, nonlinear_fraction=0.2,
+                      nonlinear_levels=(0,))
+    streams = [torch.cuda.Stream() for _ in insts]
+    setups = [instance_setup(meshes, inst, s) for inst, s in zip(insts, streams)]
+    torch.cuda.synchronize()  # inputs were written on torch's stream
+    rc, status, stats = api.mg_batch_solve([s[0] for s in setups], [i.N for i in insts], [i.T for i in insts],
+                                           [s[2] for s in setups], [s[3] for s in setups], [s[1] for s in setups])
+    assert rc == 0, status
+    together = [s[3].clone() for s in setups]
+    torch.cuda.synchronize()
+    for (ctx, opts, a0, out), inst in zip(setups, insts):
+        out.zero_()
+        torch.cuda.synchronize()
+        r, _ = ctx.mg_solve(inst.N, inst.T, a0, out, opts, allow=(-7,))
+        assert r == 0
+    torch.cuda.synchronize()
+    for (ctx, opts, a0, out), tog in zip(setups, together):
+        assert torch.equal(out, tog)
+        ctx.close()
+    assert all(s["iters"] >= 1 for s in stats)
+
+
+def test_batch_solve_rejects_repeated_context(meshes):
+    inst = instances(1, seed=0, mesh_levels=(0,), Ns=(64,), T=2.5e-3, nonlinear_fraction=0.0)[0]
+    ctx, opts, a0, out = instance_setup(meshes, inst, torch.cuda.Stream())
+    rc, _, _ = api.mg_batch_solve([ctx, ctx], [64, 64], [inst.T, inst.T], [a0, a0], [out, out], [opts, opts])
+    assert rc == -1
+    ctx.close()
