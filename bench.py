@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--path", type=int, default=0, help="with --profile-step: 0 auto, 1 cluster, 2 graph")
     ap.add_argument("--reps", type=int, default=2, help="with --profile-step: number of steps")
     ap.add_argument("--level", type=int, default=2, help="with --profile-step: mesh level 0..3 (18,240 DOFs = 2)")
+    ap.add_argument("--no-autotune", action="store_true", help="use the library's default launch shapes")
+    ap.add_argument("--instances", type=int, default=0, metavar="M",
+                    help="only the batching workload: M uneven instances, concurrent vs one by one")
     return ap.parse_args()
 
 
@@ -144,6 +147,58 @@ def profile_step(args):
     print(json.dumps({"profile_step": k, "level": args.level, "dofs": ns[0], "precision": args.precision,
                       "ms": ms, "pcg_iters_per_column": it_col, "algorithmic_bytes": alg,
                       "algorithmic_gbs": alg / ms / 1e6}))
+
+
+def instances_run(args):
+    """The batching workload: M seeded uneven machine instances (meshes of 1,104 /
+    4,512 / 18,240 DOFs, N of 256 / 512 / 1,024 steps over 5 ms, 5/10/20 kHz
+    carriers, J0 in [0.5e6, 3e6], half of the 1,104-DOF ones with the Brauer law),
+    each a 2-level FCF MGRIT solve (m = 16, tolerance 1e-6, FP32+refinement for
+    linear instances, FP64 Newton for nonlinear ones), solved concurrently by
+    mg_batch_solve and one by one; aggregate step-solves per second of both."""
+    import torch
+
+    import synth
+    from synth.model import PwmSpec, machine_model
+    from synth.workloads import instances
+    from paper_1912_03106_gb300 import api
+
+    meshes = synth.mesh_hierarchy(3)
+    insts = instances(args.instances, seed=0, mesh_levels=(0, 1, 2), Ns=(256, 512, 1024), T=5.0e-3,
+                      nonlinear_fraction=0.5, nonlinear_levels=(0,))
+    setups = []
+    for inst in insts:
+        model = machine_model(nonlinear=inst.nonlinear, pwm=PwmSpec(J0=inst.J0, f_carrier=inst.f_carrier))
+        ctx = api.Context(0, stream=torch.cuda.Stream())
+        ids = api.setup_machine(ctx, meshes[:inst.mesh_level + 1], model)
+        lv = ids[inst.mesh_level]
+        n = ctx.mg_num_dofs(lv)
+        opts = api.mgrit_opts(levels=2, m=(16,), space_level=(lv, lv), relax=1, tol=1e-6, max_iter=30,
+                              solver=api.solver_opts(precision=0 if inst.nonlinear else 1))
+        setups.append((ctx, opts, torch.zeros(n, dtype=torch.float64, device="cuda"),
+                       torch.zeros((inst.N + 1, n), dtype=torch.float64, device="cuda")))
+    torch.cuda.synchronize()
+    args_b = ([s[0] for s in setups], [i.N for i in insts], [i.T for i in insts], [s[2] for s in setups],
+              [s[3] for s in setups], [s[1] for s in setups])
+    api.mg_batch_solve(*args_b)  # warm-up: plans, step operators, PWM tables
+    t0 = time.perf_counter()
+    rc, status, stats = api.mg_batch_solve(*args_b)
+    t_conc = time.perf_counter() - t0
+    solves = sum(s["step_solves"] for s in stats)
+    t0 = time.perf_counter()
+    for (ctx, opts, a0, out), inst in zip(setups, insts):
+        ctx.mg_solve(inst.N, inst.T, a0, out, opts, allow=(-7,))
+        torch.cuda.current_stream().wait_stream(ctx.stream)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    print(json.dumps({"instances": len(insts), "status": rc,
+                      "mix": {"dofs": [s[2].numel() for s in setups], "N": [i.N for i in insts],
+                              "nonlinear": [i.nonlinear for i in insts]},
+                      "step_solves": solves, "concurrent_s": t_conc, "one_by_one_s": t_seq,
+                      "concurrent_step_solves_per_s": solves / t_conc, "one_by_one_step_solves_per_s": solves / t_seq,
+                      "speedup": t_seq / t_conc}))
+    for s in setups:
+        s[0].close()
 
 
 def dist_info():
@@ -272,6 +327,18 @@ def run_ours(args, rank, world, local):
     a0 = torch.zeros(n, dtype=torch.float64, device=dev)
     out = torch.empty((N + 1, n), dtype=torch.float64, device=dev)
 
+    # launch shapes: the library's autotuner, once per (mesh, columns) the solve and
+    # the sequential baseline use (level-0 batches of 256 columns and single steps
+    # on the 18,240-DOF mesh; 256-, 16- and 1-column batches on the 1,104-DOF mesh)
+    tuned = {}
+    if not args.no_autotune:
+        for lvl, kk in ((2, N // 16), (2, 1), (0, N // 16), (0, N // 256), (0, 1)):
+            so, ms = ctx.mg_autotune(ids[lvl], N // (1 if lvl == 2 else 16), T, kk)
+            tuned["%d_DOFs_x%d" % (ctx.mg_num_dofs(ids[lvl]), kk)] = {
+                "path": "graph" if so.path == 2 else "cluster", "tile": so.tile, "cluster": so.cluster,
+                "rows_per_block": so.rows_per_block, "coarse_rows_per_block": so.coarse_rows_per_block,
+                "base_tiles": so.base_tiles, "ms": round(ms, 4)}
+
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
@@ -390,6 +457,7 @@ def run_ours(args, rank, world, local):
         "roofline": roof,
         "clocks": clocks.summary(),
         "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "autotune": tuned,
         "wall_check_s": wall,
     }
     if rank == 0:
@@ -409,17 +477,20 @@ def roofline(ctx, ids, N, T, stream):
     events and relate its algorithmic bytes to the measured HBM copy bandwidth."""
     import torch
 
+    from paper_1912_03106_gb300 import api
+
     n = ctx.mg_num_dofs(ids[2])
     k = 256
     x_in, x_out = step_inputs(ctx, ids, k)
-    ctx.mg_step(ids[2], N, T, x_in, x_out, i0=1, istride=1)
+    so = api.solver_opts(path=2)  # the library's own graph-path shape, as in the DRAM capture
+    ctx.mg_step(ids[2], N, T, x_in, x_out, i0=1, istride=1, solver=so)
     reps = 5
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     iters = 0
     for _ in range(reps):
-        _, st = ctx.mg_step(ids[2], N, T, x_in, x_out, i0=1, istride=1)
+        _, st = ctx.mg_step(ids[2], N, T, x_in, x_out, i0=1, istride=1, solver=so)
         iters += st["cg_iters"]
     e1.record(stream)
     torch.cuda.synchronize()
@@ -513,6 +584,9 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    if args.instances:
+        instances_run(args)
+        return
     if args.profile_step:
         profile_step(args)
         return
