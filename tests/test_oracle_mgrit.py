@@ -143,3 +143,94 @@ def test_three_level_vcycle(meshes, model):
     u, h = P.mgrit(gamma=1, tol=1e-12, max_iter=30)
     assert len(h) - 1 < 16  # far faster than the exactness bound N/(2m) = 16
     assert rel_err_per_point(u, useq).max() <= 1e-9
+
+
+# ------------------------------------------------------------------ F-cycles and nested iterations
+
+class _Pow:
+    """u -> a^p u with a counter (exact coarse propagators: p = m^l)."""
+
+    def __init__(self, a, calls):
+        self.a = a
+        self.calls = calls
+
+    def __call__(self, u_prev, i):
+        self.calls[0] += 1
+        return self.a * u_prev
+
+
+def _scalar_levels(lam, dt, m, N, L, exact_coarse=False, calls=None):
+    calls = calls if calls is not None else [0]
+    phi = 1.0 / (1.0 - lam * dt)
+    levels = []
+    for l in range(L):
+        a = phi ** (m ** l) if exact_coarse else 1.0 / (1.0 - lam * dt * m ** l)
+        last = l == L - 1
+        levels.append(mgrit.Level(phi=_Pow(a, calls), N=N // m ** l, m=None if last else m,
+                                  transfer=None if last else scalar._Identity()))
+    return levels, calls
+
+
+def test_fcycle_on_two_levels_is_the_vcycle():
+    lv, _ = _scalar_levels(-50.0, 0.01, 4, 64, 2)
+    u_v, h_v = mgrit.mgrit(lv, np.array([1.0]), gamma=1, tol=0.0, max_iter=3, tol_relative=False)
+    u_f, h_f = mgrit.mgrit(lv, np.array([1.0]), gamma=1, tol=0.0, max_iter=3, tol_relative=False, cycle_kind="F")
+    assert np.array_equal(u_v, u_f) and h_v == h_f
+
+
+@pytest.mark.parametrize("gamma,bound", [(0, 64 // 4), (1, 64 // 8)])
+def test_fcycle_exactness(gamma, bound):
+    """F- and FCF-relaxation propagate exact values (Sec. 2.1): after N/m (F) or
+    N/(2m) (FCF) iterations the F-cycle iterate is the sequential solution."""
+    lv, _ = _scalar_levels(-50.0, 0.01, 4, 64, 3)
+    u, _ = mgrit.mgrit(lv, np.array([1.0]), gamma=gamma, tol=0.0, max_iter=bound, tol_relative=False,
+                       cycle_kind="F")
+    exact = (1.0 / (1.0 + 50.0 * 0.01)) ** np.arange(65)
+    assert np.abs(u[:, 0] - exact).max() <= 1e-13
+
+
+def test_fcycle_work_per_iteration():
+    """Three levels, FCF: an F-cycle iteration does exactly one extra level-1
+    V-cycle body (relaxation, residual, FAS right-hand side on level 2, the
+    sequential level-2 solve, post F-relaxation) beyond the V-cycle iteration."""
+    m, N = 4, 64
+    counts = {}
+    for kind in ("V", "F"):
+        lv, calls = _scalar_levels(-50.0, 0.01, m, N, 3)
+        g = np.zeros((N + 1, 1))
+        g[0] = 1.0
+        u = np.zeros_like(g)
+        u[0] = 1.0
+        mgrit.relax(lv[0], u, g, 1)
+        r = mgrit.cpoint_residual(lv[0], u, g)
+        calls[0] = 0
+        mgrit.coarse_correction(lv, 0, u, g, r, 1, kind)
+        counts[kind] = calls[0]
+    N1, N2 = N // m, N // m ** 2
+    NT1 = N1 // m
+    v_body = (2 * m - 1) * NT1 + NT1 + N2 + N2 + (m - 1) * NT1
+    assert counts["F"] - counts["V"] == v_body
+
+
+def test_nested_iterations_exact_with_exact_coarse_propagators():
+    """With coarse propagators equal to phi^(m^l), every level's own problem has
+    the fine solution at its points, so the nested-iteration guess is exact."""
+    lam, dt, m, N = -30.0, 0.01, 4, 256
+    lv, _ = _scalar_levels(lam, dt, m, N, 4, exact_coarse=True)
+    u = mgrit.nested_guess(lv, np.array([1.0]), gamma=1)
+    exact = (1.0 / (1.0 - lam * dt)) ** np.arange(N + 1)
+    assert np.abs(u[:, 0] - exact).max() <= 1e-14
+    _, hist = mgrit.mgrit(lv, np.array([1.0]), gamma=1, tol=0.0, max_iter=0, tol_relative=False, nested=True)
+    assert hist[0] <= 1e-14
+
+
+def test_nested_iterations_two_levels_closed_form():
+    """Two levels: the guess at C-points is the coarse sequential solution
+    phi_c^c u_0, and the F-points follow by fine steps from it."""
+    lam, dt, m, N = -20.0, 0.01, 8, 64
+    lv, _ = _scalar_levels(lam, dt, m, N, 2)
+    u = mgrit.nested_guess(lv, np.array([2.0]), gamma=1)
+    phi, phic = 1.0 / (1.0 - lam * dt), 1.0 / (1.0 - lam * dt * m)
+    for i in range(N + 1):
+        c, j = divmod(i, m)
+        assert abs(u[i, 0] - 2.0 * phic ** c * phi ** j) <= 1e-14
