@@ -256,10 +256,15 @@ typedef struct {
     int max_iter;
     int restrict_mode;     /* residual R_s: 0 injection, 1 P^T, 2 diag(P^T 1)^-1 P^T      */
     mg_solver_opts solver;
+    int cycle;             /* 0: V-cycle; 1: F-cycle (Sec. 2.1: the coarse system solved by an
+                              F-cycle and then a V-cycle on the coarse level)                */
+    int nested;            /* 1: initial guess by nested iterations (Sec. 2.1): the coarsest
+                              level's problem solved, then level by level interpolated to the
+                              C-points, F-relaxed and, below the finest, one V-cycle        */
 } mg_opts;
 
 /* Fill opts with defaults: 2 levels, m = 16, FCF, tol 1e-10 relative,
- * max_iter 50, restrict_mode 2, mg_solver_defaults(). */
+ * max_iter 50, restrict_mode 2, mg_solver_defaults(), V-cycles, zero initial guess. */
 void mg_opts_defaults(mg_opts* opts);
 
 /* FAS-MGRIT (Algorithm 1 with recursive V-cycles) for A u = g, g = (a0, 0, ..., 0)

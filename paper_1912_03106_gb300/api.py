@@ -46,7 +46,7 @@ def solver_opts(**kw) -> L.mg_solver_opts:
 
 
 def mgrit_opts(levels=2, m=(16,), space_level=(0, 0), relax=1, tol=1e-10, tol_relative=True, max_iter=50,
-               restrict_mode=2, solver: L.mg_solver_opts | None = None) -> L.mg_opts:
+               restrict_mode=2, solver: L.mg_solver_opts | None = None, cycle="V", nested=False) -> L.mg_opts:
     lib = L.load()
     o = L.mg_opts()
     lib.mg_opts_defaults(C.byref(o))
@@ -60,6 +60,8 @@ def mgrit_opts(levels=2, m=(16,), space_level=(0, 0), relax=1, tol=1e-10, tol_re
     o.tol_relative = int(bool(tol_relative))
     o.max_iter = max_iter
     o.restrict_mode = restrict_mode
+    o.cycle = {"V": 0, "F": 1}[cycle]
+    o.nested = int(bool(nested))
     if solver is not None:
         o.solver = solver
     return o

@@ -138,6 +138,32 @@ __global__ void k_correct(int64_t nf, int64_t NT, double* __restrict__ U0, int64
     }
 }
 
+// Nested iterations: C-points c = 1..NT of the fine level <- P_s v_c of the coarse
+// level's iterate (identity when the meshes agree).
+__global__ void k_interp_cpoints(int64_t nf, int64_t NT, LevelView Fv, int64_t m, LevelView Cv,
+                                 const int32_t* __restrict__ p_ptr, const int32_t* __restrict__ p_col,
+                                 const double* __restrict__ p_val) {
+    const int64_t total = nf * NT;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / NT, c = q % NT + 1;
+        double v;
+        if (p_ptr) {
+            v = 0.0;
+            for (int32_t k = p_ptr[i]; k < p_ptr[i + 1]; ++k) v += p_val[k] * Cv.base[Cv.idx(c, p_col[k])];
+        } else {
+            v = Cv.base[Cv.idx(c, i)];
+        }
+        Fv.base[Fv.idx(c * m, i)] = v;
+    }
+}
+
+// dst[j] = src[inj[j]] (nodal injection of a state), or a copy without inj
+__global__ void k_gather_state(int64_t nc, const int32_t* __restrict__ inj, const double* __restrict__ src,
+                               double* __restrict__ dst) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < nc) dst[j] = src[inj ? inj[j] : j];
+}
+
 // Level store -> time-major trajectory.
 __global__ void k_to_time_major(int64_t n, int64_t N, LevelView Uv, double* __restrict__ out) {
     const int64_t total = n * (N + 1);
@@ -249,7 +275,9 @@ struct Solver {
             phi(l, 1, L.U + (t - 1) * L.n, 1, L.U + t * L.n, 1, L.G + t * L.n, 1, t * L.stride, 0);
     }
 
-    void coarse_correction(int l) {
+    // kind 0: V-cycle, 1: F-cycle (the coarse system solved by an F-cycle and then
+    // a V-cycle on the coarse level; one solve when that level is the coarsest)
+    void coarse_correction(int l, int kind = 0) {
         Level& F = lv[l];
         Level& C = lv[l + 1];
         // restriction into the coarse mesh's node-major W, g2 (columns = coarse points)
@@ -277,7 +305,8 @@ struct Solver {
         k_fas_rhs<<<nblk(C.n * (C.N + 1)), 256, 0, c->stream>>>(C.n, C.N, C.W, C.g2, C.Vc, C.ldw, C.gview(), C.view());
         cnt.launches += 1;
         MG_CUDA(cudaGetLastError());
-        cycle(l + 1);
+        if (kind == 1 && l + 1 < (int)lv.size() - 1) cycle(l + 1, 1);
+        cycle(l + 1, 0);
         k_correct<<<nblk(F.n * F.NT), 256, 0, c->stream>>>(F.n, F.NT, F.U, F.ld, C.view(), C.W, C.ldw,
                                                           tr ? tr->P_ptr.as<int32_t>() : nullptr,
                                                           tr ? tr->P_col.as<int32_t>() : nullptr,
@@ -286,16 +315,65 @@ struct Solver {
         MG_CUDA(cudaGetLastError());
     }
 
-    void cycle(int l) {
+    void cycle(int l, int kind = 0) {
         if (l == (int)lv.size() - 1) {
             sequential_level(l);
             return;
         }
         relax(l);
         residual(l);
-        coarse_correction(l);
+        coarse_correction(l, kind);
         f_relax(l);
     }
+
+    // Nested iterations (Sec. 2.1): the coarsest level's own problem
+    // A_L(u) = (R_s a0, 0, ..., 0) solved sequentially, then towards the finest:
+    // interpolate to the C-points, F-relax, and one V-cycle below the finest.
+    // a0 already sits at point 0 of level 0; the other levels' stores are
+    // overwritten.
+    void nested_guess(const double* a0) {
+        const int L = (int)lv.size();
+        // a0 on every level's mesh (nodal injection), at point 0 of U and G
+        std::vector<const double*> a0l(L, nullptr);
+        a0l[0] = a0;
+        for (int l = 1; l < L; ++l) {
+            Level& P = lv[l - 1];
+            Level& C = lv[l];
+            const size_t gsz = C.m ? (size_t)C.m * C.n * C.ld : (size_t)(C.N + 1) * C.n;
+            MG_CUDA(cudaMemsetAsync(C.G, 0, gsz * sizeof(double), c->stream));
+            MG_CUDA(cudaMemsetAsync(C.U, 0, gsz * sizeof(double), c->stream));
+            // point 0 of the time-major coarsest store is its first n values; of a slab store, column 0
+            double* tmp = C.R ? C.R : C.U + C.n;  // scratch of at least n doubles
+            k_gather_state<<<nblk(C.n), 256, 0, c->stream>>>(C.n, P.tr ? P.tr->inj.as<int32_t>() : nullptr,
+                                                             a0l[l - 1], tmp);
+            if (C.m) {
+                k_fill_column<<<nblk(C.n), 256, 0, c->stream>>>(C.n, tmp, C.U, C.ld);
+                k_fill_column<<<nblk(C.n), 256, 0, c->stream>>>(C.n, tmp, C.G, C.ld);
+            } else {
+                MG_CUDA(cudaMemcpyAsync(C.G, tmp, C.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+                MG_CUDA(cudaMemcpyAsync(C.U, tmp, C.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            }
+            cnt.launches += 3;
+            // a contiguous copy of a0 on this mesh for the next gather
+            if (!a0stage[l].p || a0stage[l].bytes < C.n * sizeof(double)) a0stage[l].ensure(C.n * sizeof(double));
+            MG_CUDA(cudaMemcpyAsync(a0stage[l].p, tmp, C.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            a0l[l] = a0stage[l].as<double>();
+        }
+        sequential_level(L - 1);
+        for (int l = L - 2; l >= 0; --l) {
+            Level& F = lv[l];
+            Level& C = lv[l + 1];
+            const Transfer* tr = F.tr;
+            k_interp_cpoints<<<nblk(F.n * F.NT), 256, 0, c->stream>>>(
+                F.n, F.NT, F.view(), F.m, C.view(), tr ? tr->P_ptr.as<int32_t>() : nullptr,
+                tr ? tr->P_col.as<int32_t>() : nullptr, tr ? tr->P_val.as<double>() : nullptr);
+            cnt.launches += 1;
+            MG_CUDA(cudaGetLastError());
+            f_relax(l);
+            if (l > 0) cycle(l, 0);
+        }
+    }
+    DBuf a0stage[8];
 
     double read_norm() {
         double h = 0.0;
@@ -396,7 +474,8 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
     else mg_opts_defaults(&o);
     check_solver_opts(o.solver);
     if (N <= 0 || !(T > 0.0) || !a0 || !out || o.levels < 1 || o.levels > 8 || o.relax < 0 || o.relax > 4 ||
-        o.max_iter < 0 || !(o.tol >= 0.0) || o.restrict_mode < 0 || o.restrict_mode > 2)
+        o.max_iter < 0 || !(o.tol >= 0.0) || o.restrict_mode < 0 || o.restrict_mode > 2 || o.cycle < 0 ||
+        o.cycle > 1 || o.nested < 0 || o.nested > 1)
         mg_fail(MG_EINVAL, "mg_solve: bad arguments");
     auto t0 = clk::now();
     ctx_finalize(c);
@@ -497,6 +576,7 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
     k_fill_column<<<nblk(L0.n), 256, 0, c->stream>>>(L0.n, a0, L0.U, L0.ld);
     S.cnt.launches += 1;
     MG_CUDA(cudaGetLastError());
+    if (o.nested) S.nested_guess(a0);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     MG_CUDA(cudaStreamSynchronize(c->stream));
     auto t1 = clk::now();
@@ -519,7 +599,7 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
             break;
         }
         if (!(rn == rn) || it >= o.max_iter) break;
-        S.coarse_correction(0);
+        S.coarse_correction(0, o.cycle);
     }
     k_to_time_major<<<nblk(L0.n * (N + 1)), 256, 0, c->stream>>>(L0.n, N, L0.view(), out);
     S.cnt.launches += 1;

@@ -82,6 +82,8 @@ class mg_opts(C.Structure):
         ("max_iter", C.c_int),
         ("restrict_mode", C.c_int),
         ("solver", mg_solver_opts),
+        ("cycle", C.c_int),
+        ("nested", C.c_int),
     ]
 
 

@@ -245,6 +245,45 @@ def test_three_level_vcycle_with_sc(meshes, lin5k):
     assert np.all(np.abs(h - np.array(hist[:4])) <= 1e-6 * np.array(hist[:4]))
 
 
+@pytest.mark.parametrize("space,nested", [((0, 0, 0, 0), False), ((1, 0, 0, 0), False), ((1, 1, 0, 0), True),
+                                          ((0, 0, 0, 0), True)])
+def test_four_level_fcycle_follows_oracle(meshes, lin5k, space, nested):
+    """Four-level F-cycles with FCF-relaxation (m = 4, N = 256), without spatial
+    coarsening, with direct and with delayed spatial coarsening, zero or
+    nested-iteration initial guess: residual history of the first iterations
+    as the oracle's, result as sequential stepping."""
+    model, ctx, ids = lin5k
+    N, T = 256, 5e-3
+    P = MachineProblem(meshes, model, N, T, space, (4, 4, 4))
+    ref = P.sequential()
+    opts = api.mgrit_opts(levels=4, m=(4, 4, 4), space_level=tuple(ids[s] for s in space), relax=1, tol=1e-8,
+                          max_iter=40, cycle="F", nested=nested)
+    got, st = run_mgrit(ctx, N, T, ref.shape[1], opts)
+    assert rel_err_per_point(got, ref).max() <= 1e-9
+    _, hist = P.mgrit(gamma=1, tol=0.0, max_iter=3, tol_relative=False, cycle_kind="F", nested=nested)
+    k = min(4, len(st["res_hist"]))
+    h, hc = np.array(st["res_hist"][:k]), np.array(hist[:k])
+    # absolute slack 1e-9 of the first residual: the floor the 1e-13 step solves leave
+    assert np.all(np.abs(h - hc) <= 1e-6 * hc + 1e-9 * hc[0]), (h, hc)
+
+
+def test_nested_guess_alone_matches_oracle(meshes, lin5k):
+    """max_iter = 0 with nested iterations: the returned trajectory is the nested
+    guess after one relaxation, point by point as the oracle's."""
+    model, ctx, ids = lin5k
+    N, T = 128, 5e-3 / 2
+    P = MachineProblem(meshes, model, N, T, (1, 0, 0), (4, 4))
+    u_cpu, _ = P.mgrit(gamma=1, tol=0.0, max_iter=0, tol_relative=False, nested=True)
+    opts = api.mgrit_opts(levels=3, m=(4, 4), space_level=(ids[1], ids[0], ids[0]), relax=1, tol=0.0,
+                          tol_relative=False, max_iter=0, nested=True)
+    a0 = torch.zeros(u_cpu.shape[1], dtype=torch.float64, device="cuda")
+    out = torch.empty(u_cpu.shape, dtype=torch.float64, device="cuda")
+    ctx.mg_solve(N, T, a0, out, opts, allow=(-7,))
+    scale = np.linalg.norm(u_cpu[1:], axis=1).max()
+    err = np.linalg.norm(out.cpu().numpy() - u_cpu, axis=1).max() / scale
+    assert err <= 1e-10, err
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_mgrit_on_the_graph_path(meshes, lin5k, precision):
     """64 intervals per batched step: the fine level runs on the graph path."""
