@@ -153,13 +153,16 @@ def residual_norm(r: np.ndarray) -> float:
 
 def mgrit(levels, u0: np.ndarray, gamma: int = 1, tol: float = 1e-10, max_iter: int = 100,
           tol_relative: bool = True, u_init: np.ndarray | None = None, callback=None, cycle_kind: str = "V",
-          nested: bool = False):
+          nested: bool = False, stop_fn=None):
     """Solve A u = g with g = (u0, 0, ..., 0) on levels[0].
 
     Returns (u, history) where history[k] is the residual norm after the
     relaxation of iteration k (k coarse-grid corrections before it).
     `callback(k, u)` is called after each relaxation (before the norm test).
     cycle_kind "V" or "F"; nested: initial guess by nested iterations.
+    stop_fn(u_old, u_new): when given, the stop test is stop_fn(previous
+    relaxed iterate, this one) <= tol from the second iteration on (the history
+    then holds these values, the first entry inf); the residual is not used.
     """
     if nested and len(levels) > 1:
         u_init = nested_guess(levels, u0, gamma)
@@ -176,13 +179,18 @@ def mgrit(levels, u0: np.ndarray, gamma: int = 1, tol: float = 1e-10, max_iter: 
         sequential_solve(lv, u, g)
         return u, [0.0]
     hist = []
+    prev = None
     for it in range(max_iter + 1):
         relax(lv, u, g, gamma)
         r = cpoint_residual(lv, u, g)
-        hist.append(residual_norm(r))
+        if stop_fn is None:
+            hist.append(residual_norm(r))
+        else:
+            hist.append(float("inf") if prev is None else stop_fn(prev, u))
+            prev = u.copy()
         if callback is not None:
             callback(it, u)
-        ref = hist[0] if tol_relative else 1.0
+        ref = hist[0] if (tol_relative and stop_fn is None) else 1.0
         if hist[-1] <= tol * ref or it == max_iter:
             break
         coarse_correction(levels, 0, u, g, r, gamma, cycle_kind)

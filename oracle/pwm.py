@@ -49,3 +49,22 @@ def sign_table(pwm, T: float, N: int) -> np.ndarray:
     r = reference(pwm.f_ref, pwm.mod_index, T, N)
     c = carrier(pwm.f_carrier, T, N, pwm.carrier)
     return np.sign(r - c[:, None]).astype(np.int8)
+
+
+def ramp(T: float, N: int, t_ramp: float) -> np.ndarray:
+    """Start-up factor alpha(t_i) of Sec. 3.3: 0.5 (1 - cos(pi t / t_ramp)) for
+    t < t_ramp, 1 afterwards; t_ramp = 0 means no ramp.  (The printed argument
+    pi t / 2 is read as pi t / t_ramp with t_ramp two electric periods, so that the
+    factor rises from 0 to 1 over those periods.)"""
+    t = np.arange(N + 1, dtype=np.float64) * (T / N)
+    if t_ramp <= 0.0:
+        return np.ones(N + 1)
+    return np.where(t < t_ramp, 0.5 * (1.0 - np.cos(math.pi * t / t_ramp)), 1.0)
+
+
+def waveform(pwm, T: float, N: int, kind: int = 0, t_ramp: float = 0.0) -> np.ndarray:
+    """(N+1, 3) float64 source waveform per phase at t_i: alpha(t) b_s(t) for the
+    PWM source (kind 0) or alpha(t) r_s(t) for the sine reference (kind 1), which
+    Sec. 4.1 uses as the source while nested iterations build the initial guess."""
+    base = sign_table(pwm, T, N).astype(np.float64) if kind == 0 else reference(pwm.f_ref, pwm.mod_index, T, N)
+    return base * ramp(T, N, t_ramp)[:, None]

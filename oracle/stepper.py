@@ -47,8 +47,9 @@ class BandedSPD:
 
 
 class Forcing:
-    """f(t_i) = J0 * sum_s b_s(t_i) F_s on one mesh; `signs` is the (N+1, 3) PWM table
-    of the finest time grid, fine index = level index * stride."""
+    """f(t_i) = J0 * sum_s w_s(t_i) F_s on one mesh; `signs` is the (N+1, 3) source
+    waveform of the finest time grid (the PWM table b_s, possibly times the start-up
+    ramp, or the sine reference), fine index = level index * stride."""
 
     def __init__(self, F: np.ndarray, J0: float, signs: np.ndarray, stride: int = 1):
         self.F = F
