@@ -97,6 +97,12 @@ mg_status mg_set_source(mg_ctx* ctx, int32_t region, int phase, int sign);
 mg_status mg_set_pwm(mg_ctx* ctx, double J0, double f_ref, double f_carrier, int carrier,
                      double mod_index);
 
+/* Start-up ramp of the source (Sec. 3.3, used with the nonlinear law): the
+ * source waveform is multiplied by 0.5 (1 - cos(pi t / t_ramp)) for t < t_ramp
+ * (the paper's two electric periods: t_ramp = 2 / f_ref); 0 switches it off (the
+ * default).  Applies to the PWM source and to the sine reference. */
+mg_status mg_set_ramp(mg_ctx* ctx, double t_ramp);
+
 /* Assemble all meshes (P1 stiffness, consistent mass, phase loads) on the device.
  * Called implicitly by the first solve; returns MG_ENOTSPD if an operator has a
  * non-positive diagonal. */
@@ -258,9 +264,15 @@ typedef struct {
     mg_solver_opts solver;
     int cycle;             /* 0: V-cycle; 1: F-cycle (Sec. 2.1: the coarse system solved by an
                               F-cycle and then a V-cycle on the coarse level)                */
-    int nested;            /* 1: initial guess by nested iterations (Sec. 2.1): the coarsest
+    int nested;            /* initial guess by nested iterations (Sec. 2.1): the coarsest
                               level's problem solved, then level by level interpolated to the
-                              C-points, F-relaxed and, below the finest, one V-cycle        */
+                              C-points, F-relaxed and, below the finest, one V-cycle; 1 with
+                              the PWM source, 2 with the sine reference as the source
+                              (Sec. 4.1); 0: zero initial guess                              */
+    int stop_rule;         /* 0: relative or absolute residual norm (tol, tol_relative); 1: the
+                              maximal relative change of the Joule losses at C-points between
+                              two iterations <= tol (Sec. 5.1); res_hist then holds that
+                              change (the first entry infinite)                            */
 } mg_opts;
 
 /* Fill opts with defaults: 2 levels, m = 16, FCF, tol 1e-10 relative,
@@ -289,6 +301,12 @@ mg_status mg_solve(mg_ctx* ctx, int64_t N, double T, const double* a0, double* o
 mg_status mg_batch_solve(mg_ctx* const* ctxs, int n, const int64_t* N, const double* T,
                          const double* const* a0, double* const* out, const mg_opts* opts,
                          int max_threads, mg_status* status, mg_stats* stats);
+
+/* Joule losses (Eq. losses, per unit depth) of a trajectory on mesh `level`:
+ * losses[i] = d_i^T M_sigma d_i with d_i = (traj[i] - traj[i-1]) / (T/N) for
+ * i = 1..N and losses[0] = 0.  traj: (N+1)*n doubles, time-major; losses: N+1
+ * doubles (device pointers, caller-owned).  Asynchronous on the stream. */
+mg_status mg_joule_losses(mg_ctx* ctx, int level, int64_t N, double T, const double* traj, double* losses);
 
 /* As mg_solve / mg_sequential with HOST a0 and out: the call copies a0 to the
  * device, solves, and copies the trajectory back (both copies on the stream). */

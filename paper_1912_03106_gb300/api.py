@@ -46,7 +46,8 @@ def solver_opts(**kw) -> L.mg_solver_opts:
 
 
 def mgrit_opts(levels=2, m=(16,), space_level=(0, 0), relax=1, tol=1e-10, tol_relative=True, max_iter=50,
-               restrict_mode=2, solver: L.mg_solver_opts | None = None, cycle="V", nested=False) -> L.mg_opts:
+               restrict_mode=2, solver: L.mg_solver_opts | None = None, cycle="V", nested=False,
+               stop="residual") -> L.mg_opts:
     lib = L.load()
     o = L.mg_opts()
     lib.mg_opts_defaults(C.byref(o))
@@ -61,7 +62,8 @@ def mgrit_opts(levels=2, m=(16,), space_level=(0, 0), relax=1, tol=1e-10, tol_re
     o.max_iter = max_iter
     o.restrict_mode = restrict_mode
     o.cycle = {"V": 0, "F": 1}[cycle]
-    o.nested = int(bool(nested))
+    o.nested = 2 if nested == "reference" else int(bool(nested))
+    o.stop_rule = {"residual": 0, "joule": 1}[stop]
     if solver is not None:
         o.solver = solver
     return o
@@ -139,6 +141,14 @@ class Context:
 
     def mg_set_pwm(self, J0, f_ref, f_carrier, carrier, mod_index):
         self._check(self.lib.mg_set_pwm(self.h, J0, f_ref, f_carrier, carrier, mod_index))
+
+    def mg_set_ramp(self, t_ramp):
+        self._check(self.lib.mg_set_ramp(self.h, t_ramp))
+
+    def mg_joule_losses(self, level, N, T, traj, losses):
+        _dev64(traj, "traj")
+        _dev64(losses, "losses")
+        self._check(self.lib.mg_joule_losses(self.h, level, N, T, _ptr(traj), _ptr(losses)))
 
     def mg_finalize(self):
         self._check(self.lib.mg_finalize(self.h))

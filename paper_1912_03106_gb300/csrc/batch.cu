@@ -59,7 +59,7 @@ struct CallArgs {
     int64_t ld_guess;
     double* xout;
     int64_t ld_out;
-    const int8_t* signs;
+    const double* wave;
     int64_t t0, tstride;
     int k;
     double tol2;        // FP64 form: cg_tol^2; FP32+refine: refine_tol^2
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
     double sg[3] = {0.0, 0.0, 0.0};
     if (valid) {
         const int64_t tt = ca->t0 + (int64_t)gc * ca->tstride;
-        for (int q = 0; q < 3; ++q) sg[q] = (double)ca->signs[3 * tt + q];
+        for (int q = 0; q < 3; ++q) sg[q] = ca->wave[3 * tt + q];
     }
     const double* xprev = ca->xprev;
     const double* guess = ca->guess;
@@ -1309,7 +1309,7 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
     a.ld_guess = io.ld_guess;
     a.xout = io.xout;
     a.ld_out = io.ld_out;
-    a.signs = io.signs;
+    a.wave = io.wave;
     a.t0 = io.t0;
     a.tstride = io.tstride;
     a.k = io.k;

@@ -150,6 +150,10 @@ struct mg_ctx {
     DBuf pwm_table;
     int64_t pwm_N = -1;
     double pwm_T = 0.0;
+    // source waveform tables per (N, T, kind): kind 0 PWM signs, 1 sine reference,
+    // both times the start-up ramp over the first t_ramp seconds (0: none)
+    double t_ramp = 0.0;
+    std::map<std::pair<std::pair<int64_t, double>, int>, DBuf> waves;
     // reusable workspaces
     DBuf ws[32];       // step-solver work vectors
     DBuf host_in, host_out;  // staging of the *_host entry points
@@ -173,9 +177,11 @@ void ctx_finalize(mg_ctx* c);
 StepOp& ctx_step_op(mg_ctx* c, int mesh, double dt);
 Transfer& ctx_transfer(mg_ctx* c, int fine, int coarse);
 const int8_t* ctx_pwm_table(mg_ctx* c, int64_t N, double T);
+const double* ctx_wave_table(mg_ctx* c, int64_t N, double T, int kind);
 // Lookups that never allocate: null if the operator / PWM table was not built yet.
 const StepOp* ctx_find_step_op(const mg_ctx* c, int mesh, double dt);
 const int8_t* ctx_find_pwm_table(const mg_ctx* c, int64_t N, double T);
+const double* ctx_find_wave_table(const mg_ctx* c, int64_t N, double T, int kind);
 
 // ---- batched backward-Euler step (pcg.cu)
 struct PhiIO {
@@ -188,7 +194,7 @@ struct PhiIO {
     int64_t ld_guess = 0;
     double* xout = nullptr;
     int64_t ld_out = 0;
-    const int8_t* signs = nullptr;  // (N+1) x 3 PWM table of the fine grid
+    const double* wave = nullptr;   // (N+1) x 3 source waveform of the fine grid (PWM signs x ramp, or reference)
     int64_t t0 = 0, tstride = 0;    // fine time index of column c: t0 + c * tstride
 };
 

@@ -164,6 +164,67 @@ __global__ void k_gather_state(int64_t nc, const int32_t* __restrict__ inj, cons
     if (j < nc) dst[j] = src[inj ? inj[j] : j];
 }
 
+// Joule losses (Eq. losses, per unit depth): P = d^T M_sigma d with d = (u_t - u_{t-1}) / dt.
+// One block per time point; UV gives u_t, PV u_{t-1}; a fixed-order block sum.
+__device__ void joule_block(int64_t n, LevelView Uv, int64_t t, int64_t tp, const int32_t* __restrict__ rp,
+                            const int32_t* __restrict__ col, const double* __restrict__ M, double inv_dt,
+                            double* out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        const double dr = (Uv.base[Uv.idx(t, r)] - Uv.base[Uv.idx(tp, r)]) * inv_dt;
+        double md = 0.0;
+        for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
+            const int64_t j = col[k];
+            md += M[k] * ((Uv.base[Uv.idx(t, j)] - Uv.base[Uv.idx(tp, j)]) * inv_dt);
+        }
+        acc += dr * md;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// losses at every time point of a trajectory (block t-1 -> point t, t = 1..N)
+__global__ void k_joule_traj(int64_t n, LevelView Uv, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const double* __restrict__ M, double inv_dt, double* out) {
+    const int64_t t = blockIdx.x + 1;
+    joule_block(n, Uv, t, t - 1, rp, col, M, inv_dt, out + t);
+}
+
+// losses at the C-points c = 1..NT of a level store (point cm from cm-1)
+__global__ void k_joule_cpoints(int64_t n, LevelView Uv, int64_t m, const int32_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, const double* __restrict__ M, double inv_dt,
+                                double* out) {
+    const int64_t c = blockIdx.x + 1;
+    joule_block(n, Uv, c * m, c * m - 1, rp, col, M, inv_dt, out + c);
+}
+
+// max_c |P_new - P_old| / |P_new| into *res (infinite on the first call), then P_old = P_new
+__global__ void k_joule_change(int64_t NT, const double* __restrict__ pnew, double* __restrict__ pold, int first,
+                               double* res) {
+    __shared__ double red[256];
+    double mx = 0.0;
+    for (int64_t c = 1 + threadIdx.x; c <= NT; c += blockDim.x) {
+        const double a = pnew[c], b = pold[c];
+        const double den = a != 0.0 ? fabs(a) : 1.0;
+        mx = fmax(mx, fabs(a - b) / den);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *res = first ? INFINITY : red[0];
+    __syncthreads();
+    for (int64_t c = threadIdx.x; c <= NT; c += blockDim.x) pold[c] = pnew[c];
+}
+
 // Level store -> time-major trajectory.
 __global__ void k_to_time_major(int64_t n, int64_t N, LevelView Uv, double* __restrict__ out) {
     const int64_t total = n * (N + 1);
@@ -198,7 +259,8 @@ struct Solver {
     double T;
     mg_opts o;
     std::vector<Level> lv;
-    const int8_t* signs = nullptr;
+    const double* wave = nullptr;      // source waveform of the iterations (PWM, with the ramp)
+    const double* wave_ref = nullptr;  // sine reference (nested iterations with nested == 2)
     SolveCounters cnt;
     double* partial = nullptr;
     double* norm = nullptr;
@@ -216,7 +278,7 @@ struct Solver {
         io.ld_guess = ldo;
         io.xout = xout;
         io.ld_out = ldo;
-        io.signs = signs;
+        io.wave = wave;
         io.t0 = t0;
         io.tstride = tstride;
         phi_batch(c, *lv[l].op, io, o.solver, &cnt);
@@ -259,7 +321,7 @@ struct Solver {
         io.ld_guess = L.ld;
         io.xout = L.V;
         io.ld_out = L.ld;
-        io.signs = signs;
+        io.wave = wave;
         io.t0 = L.m * L.stride;
         io.tstride = L.m * L.stride;
         phi_batch(c, *L.op, io, o.solver, &cnt);
@@ -298,7 +360,7 @@ struct Solver {
         io.ld_guess = C.ldw;
         io.xout = C.Vc;
         io.ld_out = C.ldw;
-        io.signs = signs;
+        io.wave = wave;
         io.t0 = C.stride;
         io.tstride = C.stride;
         phi_batch(c, *C.op, io, o.solver, &cnt);
@@ -333,6 +395,8 @@ struct Solver {
     // overwritten.
     void nested_guess(const double* a0) {
         const int L = (int)lv.size();
+        const double* keep = wave;
+        if (wave_ref) wave = wave_ref;  // the sine reference as the source (Sec. 4.1)
         // a0 on every level's mesh (nodal injection), at point 0 of U and G
         std::vector<const double*> a0l(L, nullptr);
         a0l[0] = a0;
@@ -372,8 +436,31 @@ struct Solver {
             f_relax(l);
             if (l > 0) cycle(l, 0);
         }
+        wave = keep;
     }
     DBuf a0stage[8];
+
+    // maximal relative change of the level-0 C-point losses since the last call
+    double joule_change(bool first) {
+        Level& L = lv[0];
+        const MeshLevel& m = c->meshes[L.mesh];
+        joule_new.ensure((L.NT + 1) * sizeof(double));
+        joule_old.ensure((L.NT + 1) * sizeof(double));
+        joule_res.ensure(sizeof(double));
+        MG_CUDA(cudaMemsetAsync(joule_new.p, 0, sizeof(double), c->stream));
+        k_joule_cpoints<<<(unsigned)L.NT, 256, 0, c->stream>>>(L.n, L.view(), L.m, m.rowptr.as<int32_t>(),
+                                                                m.col.as<int32_t>(), m.M.as<double>(), 1.0 / L.dt,
+                                                                joule_new.as<double>());
+        k_joule_change<<<1, 256, 0, c->stream>>>(L.NT, joule_new.as<double>(), joule_old.as<double>(), first ? 1 : 0,
+                                                 joule_res.as<double>());
+        cnt.launches += 2;
+        MG_CUDA(cudaGetLastError());
+        double h = 0.0;
+        MG_CUDA(cudaMemcpyAsync(&h, joule_res.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        MG_CUDA(cudaStreamSynchronize(c->stream));
+        return h;
+    }
+    DBuf joule_new, joule_old, joule_res;
 
     double read_norm() {
         double h = 0.0;
@@ -434,7 +521,7 @@ mg_status sequential_impl(mg_ctx* c, int level, int64_t N, double T, const doubl
     ctx_finalize(c);
     const int64_t n = c->meshes[level].n;
     StepOp& op = ctx_step_op(c, level, T / (double)N);
-    const int8_t* signs = ctx_pwm_table(c, N, T);
+    const double* wave = ctx_wave_table(c, N, T, 0);
     reset_counters(c);
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
@@ -452,7 +539,7 @@ mg_status sequential_impl(mg_ctx* c, int level, int64_t N, double T, const doubl
         io.ld_guess = 1;
         io.xout = out + t * n;
         io.ld_out = 1;
-        io.signs = signs;
+        io.wave = wave;
         io.t0 = t;
         io.tstride = 0;
         phi_batch(c, op, io, so, &cnt);
@@ -475,7 +562,7 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
     check_solver_opts(o.solver);
     if (N <= 0 || !(T > 0.0) || !a0 || !out || o.levels < 1 || o.levels > 8 || o.relax < 0 || o.relax > 4 ||
         o.max_iter < 0 || !(o.tol >= 0.0) || o.restrict_mode < 0 || o.restrict_mode > 2 || o.cycle < 0 ||
-        o.cycle > 1 || o.nested < 0 || o.nested > 1)
+        o.cycle > 1 || o.nested < 0 || o.nested > 2 || o.stop_rule < 0 || o.stop_rule > 1)
         mg_fail(MG_EINVAL, "mg_solve: bad arguments");
     auto t0 = clk::now();
     ctx_finalize(c);
@@ -569,7 +656,8 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
     }
     S.partial = take(S.kRedBlocks * sizeof(double));
     S.norm = take(sizeof(double));
-    S.signs = ctx_pwm_table(c, N, T);
+    S.wave = ctx_wave_table(c, N, T, 0);
+    if (o.nested == 2) S.wave_ref = ctx_wave_table(c, N, T, 1);
     reset_counters(c);
     Level& L0 = S.lv[0];
     MG_CUDA(cudaMemsetAsync(L0.U, 0, L0.m * L0.n * L0.ld * sizeof(double), c->stream));
@@ -587,18 +675,18 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
     for (it = 0;; ++it) {
         S.relax(0);
         S.residual(0);
-        double rn = S.read_norm();
+        double rn = o.stop_rule == 1 ? S.joule_change(it == 0) : S.read_norm();
         hist.push_back(rn);
         if (mg_trace_level() >= 1)
             std::fprintf(stderr, "[mgrit] iteration %d  residual %.4e  %.3f s  step-solves %lld  newton %lld\n", it,
                          rn, secs(t1, clk::now()), (long long)S.cnt.step_solves, (long long)S.cnt.newton_iters);
         if (it == 0) r0 = rn;
-        double ref = o.tol_relative ? r0 : 1.0;
+        double ref = (o.tol_relative && o.stop_rule == 0) ? r0 : 1.0;
         if (rn <= o.tol * ref) {
             converged = true;
             break;
         }
-        if (!(rn == rn) || it >= o.max_iter) break;
+        if (rn != rn || it >= o.max_iter) break;
         S.coarse_correction(0, o.cycle);
     }
     k_to_time_major<<<nblk(L0.n * (N + 1)), 256, 0, c->stream>>>(L0.n, N, L0.view(), out);
@@ -682,7 +770,7 @@ mg_status mg_step(mg_ctx* c, int level, int64_t N, double T, int64_t dt_mult, in
             mg_fail(MG_EINVAL, "mg_step: bad arguments");
         ctx_finalize(c);
         StepOp& op = ctx_step_op(c, level, (double)dt_mult * T / (double)N);
-        const int8_t* signs = ctx_pwm_table(c, N, T);
+        const double* wave = ctx_wave_table(c, N, T, 0);
         reset_counters(c);
         auto t1 = clk::now();
         PhiIO io;
@@ -693,7 +781,7 @@ mg_status mg_step(mg_ctx* c, int level, int64_t N, double T, int64_t dt_mult, in
         io.ld_guess = ld_out;
         io.xout = x_out;
         io.ld_out = ld_out;
-        io.signs = signs;
+        io.wave = wave;
         io.t0 = i0;
         io.tstride = istride;
         SolveCounters cnt;
@@ -704,6 +792,21 @@ mg_status mg_step(mg_ctx* c, int level, int64_t N, double T, int64_t dt_mult, in
             stats->t_solve = secs(t1, clk::now());
             if (stats->worst_status != 0) return (mg_status)stats->worst_status;
         }
+        return MG_OK;
+    });
+}
+
+mg_status mg_joule_losses(mg_ctx* c, int level, int64_t N, double T, const double* traj, double* losses) {
+    return run(c, [&]() -> mg_status {
+        if (level < 0 || level >= (int)c->meshes.size() || N <= 0 || !(T > 0.0) || !traj || !losses)
+            mg_fail(MG_EINVAL, "mg_joule_losses: bad arguments");
+        ctx_finalize(c);
+        const MeshLevel& m = c->meshes[level];
+        MG_CUDA(cudaMemsetAsync(losses, 0, sizeof(double), c->stream));
+        LevelView v{const_cast<double*>(traj), m.n, 0, 0, 0};
+        k_joule_traj<<<(unsigned)N, 256, 0, c->stream>>>(m.n, v, m.rowptr.as<int32_t>(), m.col.as<int32_t>(),
+                                                          m.M.as<double>(), (double)N / T, losses);
+        MG_CUDA(cudaGetLastError());
         return MG_OK;
     });
 }

@@ -108,7 +108,7 @@ struct Step {
     const double* Kc;    // ELL stiffness of linear elements
     const double* F;     // 3 x n phase loads
     double inv_dt, J0;
-    const int8_t* signs;
+    const double* wave;
     int64_t t0, tstride;
 };
 
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(NTB) kn_resid(Step S, int64_t ne, const int32_
     double sg[3] = {0.0, 0.0, 0.0};
     if (on) {
         const int64_t tt = S.t0 + (int64_t)gc * S.tstride;
-        for (int q = 0; q < 3; ++q) sg[q] = (double)S.signs[3 * tt + q];
+        for (int q = 0; q < 3; ++q) sg[q] = S.wave[3 * tt + q];
     }
     const double* at = a + (size_t)t * S.n * G + lc;
     const double* pt = aprev + (size_t)t * S.n * G + lc;
@@ -802,7 +802,7 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
     S.F = m0.F.as<double>();
     S.inv_dt = 1.0 / op.dt;
     S.J0 = c->pwm.J0;
-    S.signs = io.signs;
+    S.wave = io.wave;
     S.t0 = io.t0;
     S.tstride = io.tstride;
     Elems E = {};

@@ -94,7 +94,7 @@ struct PcgArgs {
     double inv_dt;
     const double* F;  // 3 x n (depth 0)
     double J0;
-    const int8_t* signs;
+    const double* wave;
     int64_t t0, tstride;
     const double* xprev;
     int64_t ld_prev;
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
     double sg[3] = {0.0, 0.0, 0.0};
     if (valid) {
         const int64_t t = a.t0 + cio * a.tstride;
-        for (int q = 0; q < 3; ++q) sg[q] = (double)a.signs[3 * t + q];
+        for (int q = 0; q < 3; ++q) sg[q] = a.wave[3 * t + q];
     }
     if (threadIdx.x < KT) {
         s.act[threadIdx.x] = threadIdx.x < kc;
@@ -1032,7 +1032,7 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
     a.inv_dt = 1.0 / op.dt;
     a.F = m0.F.as<double>();
     a.J0 = c->pwm.J0;
-    a.signs = io.signs;
+    a.wave = io.wave;
     a.t0 = io.t0;
     a.tstride = io.tstride;
     a.xprev = io.xprev;
@@ -1134,8 +1134,8 @@ void static_step(void* arg) {
         mg_fail(MG_EINVAL, "mg_step_static: bad solver options");
     const double dt = (double)q.dt_mult * q.T / (double)q.N;
     const StepOp* op = ctx_find_step_op(c, q.level, dt);
-    const int8_t* signs = ctx_find_pwm_table(c, q.N, q.T);
-    if (!op || !signs)
+    const double* wave = ctx_find_wave_table(c, q.N, q.T, 0);
+    if (!op || !wave)
         mg_fail(MG_ESTATE, "mg_step_static: the step operator or PWM table for this level, N, T and dt does not exist "
                            "yet; one regular mg_step call with the same arguments builds both");
     if (mesh_is_nonlinear(c, op->mesh))
@@ -1225,7 +1225,7 @@ void static_step(void* arg) {
     a.inv_dt = 1.0 / op->dt;
     a.F = m0.F.as<double>();
     a.J0 = c->pwm.J0;
-    a.signs = signs;
+    a.wave = wave;
     a.t0 = q.i0;
     a.tstride = q.istride;
     a.xprev = q.x_in;

@@ -280,6 +280,31 @@ __global__ void k_pwm_table(int64_t N, double T_over_N, double w, double mod_ind
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Start-up factor of Sec. 3.3: 0.5 (1 - cos(pi t / t_ramp)) for t < t_ramp, else 1.
+__device__ __forceinline__ double ramp_factor(double t, double t_ramp) {
+    return (t_ramp > 0.0 && t < t_ramp) ? 0.5 * (1.0 - cos(M_PI * t / t_ramp)) : 1.0;
+}
+
+// Source waveform w_s(t_i) = alpha(t_i) b_s(t_i) from the PWM sign table.
+__global__ void k_wave_pwm(int64_t N, double T_over_N, double t_ramp, const int8_t* __restrict__ signs,
+                           double* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > N) return;
+    const double a = ramp_factor(__dmul_rn((double)i, T_over_N), t_ramp);
+    for (int s = 0; s < 3; ++s) out[3 * i + s] = a * (double)signs[3 * i + s];
+}
+
+// w_s(t_i) = alpha(t_i) r_s(t_i): the sine reference of Eq. machine_reference_signal.
+__global__ void k_wave_reference(int64_t N, double T_over_N, double w, double mod_index, double phi1, double phi2,
+                                 double t_ramp, double* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > N) return;
+    const double t = __dmul_rn((double)i, T_over_N);
+    const double a = ramp_factor(t, t_ramp);
+    const double phis[3] = {0.0, phi1, phi2};
+    for (int s = 0; s < 3; ++s) out[3 * i + s] = a * (mod_index * sin(__dadd_rn(__dmul_rn(w, t), phis[s])));
+}
+
 // ------------------------------------------------------------------ assembly
 
 static int read_flag(mg_ctx* c) {
@@ -595,6 +620,29 @@ const int8_t* ctx_pwm_table(mg_ctx* c, int64_t N, double T) {
     return c->pwm_table.as<int8_t>();
 }
 
+const double* ctx_find_wave_table(const mg_ctx* c, int64_t N, double T, int kind) {
+    auto it = c->waves.find({{N, T}, kind});
+    return it == c->waves.end() ? nullptr : it->second.as<double>();
+}
+
+const double* ctx_wave_table(mg_ctx* c, int64_t N, double T, int kind) {
+    if (const double* w = ctx_find_wave_table(c, N, T, kind)) return w;
+    if (!c->pwm.set) mg_fail(MG_ESTATE, "mg_set_pwm was not called");
+    DBuf& b = c->waves[{{N, T}, kind}];
+    b.ensure((size_t)3 * (N + 1) * sizeof(double));
+    if (kind == 0) {
+        const int8_t* sg = ctx_pwm_table(c, N, T);
+        k_wave_pwm<<<nblk(N + 1), 256, 0, c->stream>>>(N, T / (double)N, c->t_ramp, sg, b.as<double>());
+    } else {
+        const PwmSpec& p = c->pwm;
+        k_wave_reference<<<nblk(N + 1), 256, 0, c->stream>>>(N, T / (double)N, 2.0 * M_PI * p.f_ref, p.mod_index,
+                                                            -2.0 * M_PI / 3.0, -4.0 * M_PI / 3.0, c->t_ramp,
+                                                            b.as<double>());
+    }
+    MG_CUDA(cudaGetLastError());
+    return b.as<double>();
+}
+
 // ------------------------------------------------------------------ transfers
 
 // Node-space prolongation rows: fine node -> list of (coarse node, weight).
@@ -845,6 +893,15 @@ mg_status mg_set_pwm(mg_ctx* c, double J0, double f_ref, double f_carrier, int c
             mg_fail(MG_EINVAL, "mg_set_pwm: bad arguments");
         c->pwm = PwmSpec{J0, f_ref, f_carrier, mod_index, carrier, true};
         c->pwm_N = -1;
+        c->waves.clear();
+    });
+}
+
+mg_status mg_set_ramp(mg_ctx* c, double t_ramp) {
+    return guarded(c, [&] {
+        if (!(t_ramp >= 0.0) || !std::isfinite(t_ramp)) mg_fail(MG_EINVAL, "mg_set_ramp: bad arguments");
+        c->t_ramp = t_ramp;
+        c->waves.clear();
     });
 }
 

@@ -59,7 +59,7 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
             ctx_finalize(c);
             if (mesh_is_nonlinear(c, A.level)) mg_fail(MG_EINVAL, "mg_autotune: times linear steps only");
             const StepOp& op = ctx_step_op(c, A.level, A.T / (double)A.N);
-            const int8_t* signs = ctx_pwm_table(c, A.N, A.T);
+            const double* wave = ctx_wave_table(c, A.N, A.T, 0);
             const int64_t n = c->meshes[A.level].n;
             DBuf xin, xout;
             xin.ensure((size_t)n * A.k * sizeof(double));
@@ -73,7 +73,7 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
             io.ld_prev = A.k;
             io.xout = xout.as<double>();
             io.ld_out = A.k;
-            io.signs = signs;
+            io.wave = wave;
             io.t0 = std::min<int64_t>(1, A.N);
             io.tstride = A.k > 1 && io.t0 + (int64_t)(A.k - 1) <= A.N ? 1 : 0;
             cudaEvent_t e0, e1;

@@ -84,6 +84,7 @@ class mg_opts(C.Structure):
         ("solver", mg_solver_opts),
         ("cycle", C.c_int),
         ("nested", C.c_int),
+        ("stop_rule", C.c_int),
     ]
 
 
@@ -100,6 +101,7 @@ _SIGNATURES = {
     "mg_set_material": (C.c_int, [_P, C.c_int32, _D, _D, C.c_int, _D, _D, _D]),
     "mg_set_source": (C.c_int, [_P, C.c_int32, C.c_int, C.c_int]),
     "mg_set_pwm": (C.c_int, [_P, _D, _D, _D, C.c_int, _D]),
+    "mg_set_ramp": (C.c_int, [_P, _D]),
     "mg_finalize": (C.c_int, [_P]),
     "mg_num_dofs": (_I64, [_P, C.c_int]),
     "mg_get_operators": (C.c_int, [_P, C.c_int, C.POINTER(_I64), _P, _P, _P, _P, _P]),
@@ -115,6 +117,7 @@ _SIGNATURES = {
     "mg_solve_host": (C.c_int, [_P, _I64, _D, _P, _P, C.POINTER(mg_opts), C.POINTER(mg_stats)]),
     "mg_sequential_host": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P, C.POINTER(mg_solver_opts),
                                      C.POINTER(mg_stats)]),
+    "mg_joule_losses": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P]),
     "mg_autotune": (C.c_int, [_P, C.c_int, _I64, _D, C.c_int, C.POINTER(mg_solver_opts), C.POINTER(_D)]),
     "mg_batch_solve": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_I64), C.POINTER(_D), C.POINTER(_P),
                                  C.POINTER(_P), C.POINTER(mg_opts), C.c_int, C.POINTER(C.c_int),
