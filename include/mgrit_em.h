@@ -308,6 +308,26 @@ mg_status mg_batch_solve(mg_ctx* const* ctxs, int n, const int64_t* N, const dou
  * doubles (device pointers, caller-owned).  Asynchronous on the stream. */
 mg_status mg_joule_losses(mg_ctx* ctx, int level, int64_t N, double T, const double* traj, double* losses);
 
+/* Temporal coarsening plan (Sec. 4.1's heuristic, no GPU work): from measured
+ * times ms_list[i] of one batched step of k_list[i] columns, the batch width k*
+ * is the smallest one whose throughput (columns per ms) is within 90 % of the
+ * best; the first coarsening factor m0 is the largest power of two dividing N
+ * with N / m0 >= k* (at least 2), every further level coarsens by 2 while it
+ * keeps at least 2 intervals and levels < max_levels.  Writes *levels_out and
+ * m_out[0 .. levels-2] (the rest 0).  MG_EINVAL for odd N or bad input. */
+mg_status mg_choose_levels(const double* k_list, const double* ms_list, int nk, int64_t N, int max_levels,
+                           int* levels_out, int* m_out);
+
+/* Measures batched-step times on mesh fine_level for 16, 32, ..., 1024 columns
+ * (at most N/2), applies mg_choose_levels, and fills opts->levels, opts->m and
+ * opts->space_level (fine_level on the finest time level, coarse_level on the
+ * others; its other fields are kept).  iter_ms (may be NULL) receives a cost
+ * model's estimate of one FCF iteration: per level 2m batched steps of N_l/m
+ * columns, the FAS step of the next level, the coarsest level's N_L single
+ * steps, all at measured step times.  Linear meshes only (MG_EINVAL otherwise). */
+mg_status mg_plan_levels(mg_ctx* ctx, int fine_level, int coarse_level, int64_t N, double T, int max_levels,
+                         mg_opts* opts, double* iter_ms);
+
 /* As mg_solve / mg_sequential with HOST a0 and out: the call copies a0 to the
  * device, solves, and copies the trajectory back (both copies on the stream). */
 mg_status mg_solve_host(mg_ctx* ctx, int64_t N, double T, const double* a0_host,

@@ -142,6 +142,14 @@ class Context:
     def mg_set_pwm(self, J0, f_ref, f_carrier, carrier, mod_index):
         self._check(self.lib.mg_set_pwm(self.h, J0, f_ref, f_carrier, carrier, mod_index))
 
+    def mg_plan_levels(self, fine_level, coarse_level, N, T, max_levels=5, opts=None):
+        """Returns (mg_opts with levels, m, space_level filled, estimated ms per FCF iteration)."""
+        o = opts or mgrit_opts()
+        ms = C.c_double(0.0)
+        self._check(self.lib.mg_plan_levels(self.h, fine_level, coarse_level, N, T, max_levels, C.byref(o),
+                                            C.byref(ms)))
+        return o, ms.value
+
     def mg_set_ramp(self, t_ramp):
         self._check(self.lib.mg_set_ramp(self.h, t_ramp))
 
@@ -283,3 +291,18 @@ def mg_batch_solve(ctxs, N, T, a0, out, opts, max_threads=0):
     stats = (L.mg_stats * n)()
     rc = lib.mg_batch_solve(hs, n, Ns, Ts, a0p, outp, op, max_threads, st, stats)
     return rc, [L.STATUS.get(v, v) for v in st], [stats_dict(s) for s in stats]
+
+
+def mg_choose_levels(k_list, ms_list, N, max_levels=5):
+    """Sec. 4.1's coarsening heuristic on measured step times (host only).
+    Returns (levels, [m_0, ..., m_{levels-2}])."""
+    lib = L.load()
+    nk = len(k_list)
+    ks = (C.c_double * nk)(*k_list)
+    ts = (C.c_double * nk)(*ms_list)
+    lv = C.c_int(0)
+    m = (C.c_int * 8)()
+    rc = lib.mg_choose_levels(ks, ts, nk, N, max_levels, C.byref(lv), m)
+    if rc != L.MG_OK:
+        raise L.MgError(rc, "mg_choose_levels: bad input")
+    return lv.value, [m[i] for i in range(lv.value - 1)]

@@ -151,3 +151,130 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
         },
         &a);
 }
+
+// ------------------------------------------------------------------ temporal coarsening plan
+//
+// Sec. 4.1 chooses a large first coarsening factor so that the second time grid
+// has one point per processor, and factor 2 on the coarser grids.  On one GPU the
+// counterpart of "one point per processor" is the batch width from which a
+// batched step stops gaining throughput: the first factor makes the finest
+// relaxation batches that wide.
+
+extern "C" mg_status mg_choose_levels(const double* k_list, const double* ms_list, int nk, int64_t N, int max_levels,
+                                      int* levels_out, int* m_out) {
+    if (!k_list || !ms_list || nk <= 0 || N < 2 || max_levels < 2 || max_levels > 8 || !levels_out || !m_out)
+        return MG_EINVAL;
+    double best = 0.0;
+    for (int i = 0; i < nk; ++i) {
+        if (!(k_list[i] >= 1.0) || !(ms_list[i] > 0.0)) return MG_EINVAL;
+        best = std::max(best, k_list[i] / ms_list[i]);
+    }
+    double kstar = 0.0;
+    for (int i = 0; i < nk; ++i)
+        if (k_list[i] / ms_list[i] >= 0.9 * best && (kstar == 0.0 || k_list[i] < kstar)) kstar = k_list[i];
+    // first factor: the largest power of two dividing N with N / m0 >= kstar (at least 2)
+    int64_t m0 = 2;
+    while (N % (m0 * 2) == 0 && (double)(N / (m0 * 2)) >= kstar) m0 *= 2;
+    if (N % m0) return MG_EINVAL;  // N odd
+    int levels = 2;
+    m_out[0] = (int)m0;
+    int64_t Nl = N / m0;
+    while (levels < max_levels && Nl % 2 == 0 && Nl / 2 >= 2) {
+        m_out[levels - 1] = 2;
+        Nl /= 2;
+        ++levels;
+    }
+    for (int l = levels - 1; l < 8; ++l) m_out[l] = 0;
+    *levels_out = levels;
+    return MG_OK;
+}
+
+extern "C" mg_status mg_plan_levels(mg_ctx* c, int fine_level, int coarse_level, int64_t N, double T, int max_levels,
+                                    mg_opts* opts, double* iter_ms) {
+    struct Args {
+        mg_ctx* c;
+        int fine, coarse;
+        int64_t N;
+        double T;
+        int max_levels;
+        mg_opts* opts;
+        double* iter_ms;
+    } a{c, fine_level, coarse_level, N, T, max_levels, opts, iter_ms};
+    return mg_guarded_call(
+        c,
+        [](void* p) {
+            Args& A = *static_cast<Args*>(p);
+            mg_ctx* c = A.c;
+            if (!A.opts || A.fine < 0 || A.fine >= (int)c->meshes.size() || A.coarse < 0 ||
+                A.coarse >= (int)c->meshes.size() || A.N < 2 || !(A.T > 0.0))
+                mg_fail(MG_EINVAL, "mg_plan_levels: bad arguments");
+            ctx_finalize(c);
+            if (mesh_is_nonlinear(c, A.fine)) mg_fail(MG_EINVAL, "mg_plan_levels: times linear steps only");
+            // step time against batch width on the fine mesh (library shapes)
+            std::vector<double> ks, ms;
+            auto time_step = [&](int mesh, int64_t Nl, int k) {
+                const StepOp& op = ctx_step_op(c, mesh, A.T / (double)Nl);
+                const double* wave = ctx_wave_table(c, A.N, A.T, 0);
+                const int64_t n = c->meshes[mesh].n;
+                DBuf xin, xout;
+                xin.ensure((size_t)n * k * sizeof(double));
+                xout.ensure((size_t)n * k * sizeof(double));
+                kt_fill<<<(unsigned)((n * k + 255) / 256), 256, 0, c->stream>>>(n * k, xin.as<double>());
+                PhiIO io;
+                io.k = k;
+                io.xprev = xin.as<double>();
+                io.ld_prev = k;
+                io.xout = xout.as<double>();
+                io.ld_out = k;
+                io.wave = wave;
+                io.t0 = 1;
+                io.tstride = (k > 1 && 1 + (int64_t)(k - 1) * (A.N / Nl) <= A.N) ? A.N / Nl : 0;
+                mg_solver_opts so = A.opts->solver;
+                phi_batch(c, op, io, so, nullptr);
+                cudaEvent_t e0, e1;
+                MG_CUDA(cudaEventCreate(&e0));
+                MG_CUDA(cudaEventCreate(&e1));
+                MG_CUDA(cudaEventRecord(e0, c->stream));
+                for (int r = 0; r < 2; ++r) phi_batch(c, op, io, so, nullptr);
+                MG_CUDA(cudaEventRecord(e1, c->stream));
+                MG_CUDA(cudaEventSynchronize(e1));
+                float t = 0.0f;
+                MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return (double)t / 2.0;
+            };
+            for (int k = 16; k <= 1024 && k <= A.N / 2; k *= 2) {
+                ks.push_back(k);
+                ms.push_back(time_step(A.fine, A.N, k));
+            }
+            int levels = 0, m[8] = {};
+            if (mg_choose_levels(ks.data(), ms.data(), (int)ks.size(), A.N, std::max(2, A.max_levels), &levels, m) !=
+                MG_OK)
+                mg_fail(MG_EINVAL, "mg_plan_levels: N has no power-of-two coarsening");
+            // cost model of one FCF iteration: per level (2m-1) relaxation batches + the residual
+            // batch of N_l/m columns, the FAS step of the next level, the coarsest level sequential
+            double est = 0.0;
+            int64_t Nl = A.N;
+            for (int l = 0; l < levels; ++l) {
+                const int mesh = l == 0 ? A.fine : A.coarse;
+                if (l == levels - 1) {
+                    est += (double)Nl * time_step(mesh, Nl, 1);
+                    break;
+                }
+                const int k = (int)(Nl / m[l]);
+                const double tk = time_step(mesh, Nl, k);
+                est += (double)(2 * m[l]) * tk;
+                if (l + 1 < levels) est += time_step(A.coarse, Nl / m[l], (int)(Nl / m[l]));
+                Nl /= m[l];
+            }
+            ctx_drop_plans(c);
+            A.opts->levels = levels;
+            for (int l = 0; l < 8; ++l) {
+                A.opts->m[l] = l < levels - 1 ? m[l] : 0;
+                A.opts->space_level[l] = l == 0 ? A.fine : A.coarse;
+            }
+            if (A.iter_ms) *A.iter_ms = est;
+        },
+        &a);
+}

@@ -117,6 +117,9 @@ _SIGNATURES = {
     "mg_solve_host": (C.c_int, [_P, _I64, _D, _P, _P, C.POINTER(mg_opts), C.POINTER(mg_stats)]),
     "mg_sequential_host": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P, C.POINTER(mg_solver_opts),
                                      C.POINTER(mg_stats)]),
+    "mg_choose_levels": (C.c_int, [C.POINTER(_D), C.POINTER(_D), C.c_int, _I64, C.c_int, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]),
+    "mg_plan_levels": (C.c_int, [_P, C.c_int, C.c_int, _I64, _D, C.c_int, C.POINTER(mg_opts), C.POINTER(_D)]),
     "mg_joule_losses": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P]),
     "mg_autotune": (C.c_int, [_P, C.c_int, _I64, _D, C.c_int, C.POINTER(mg_solver_opts), C.POINTER(_D)]),
     "mg_batch_solve": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_I64), C.POINTER(_D), C.POINTER(_P),

@@ -58,3 +58,22 @@ def test_null_context_is_rejected(libpath):
     L = lib.load()
     assert L.mg_finalize(None) == -1  # MG_EINVAL, no CUDA call made
     assert L.mg_num_dofs(None, 0) == -1
+
+
+def test_choose_levels_heuristic():
+    """Host-only decision of the temporal coarsening plan (no GPU call)."""
+    from paper_1912_03106_gb300 import api
+
+    ks = [16, 32, 64, 128, 256, 512, 1024]
+    # throughput k / ms saturates at 256 columns
+    ms = [1.0, 1.0, 1.0, 1.1, 1.9, 3.8, 7.6]
+    levels, m = api.mg_choose_levels(ks, ms, 4096, max_levels=5)
+    assert m[0] == 16 and levels == 5 and m[1:] == [2, 2, 2]
+    # a wider saturation point gives a smaller first factor
+    levels, m = api.mg_choose_levels(ks, [1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.9], 4096, max_levels=3)
+    assert m == [8, 2] and levels == 3
+    # the coarsest level keeps at least 2 intervals
+    levels, m = api.mg_choose_levels([16], [1.0], 64, max_levels=8)
+    assert m[0] == 4 and 64 // 4 // (2 ** (levels - 2)) >= 2
+    with pytest.raises(api.L.MgError):
+        api.mg_choose_levels([16], [1.0], 63)

@@ -102,3 +102,31 @@ def test_batch_solve_rejects_repeated_context(meshes):
     rc, _, _ = api.mg_batch_solve([ctx, ctx], [64, 64], [inst.T, inst.T], [a0, a0], [out, out], [opts, opts])
     assert rc == -1
     ctx.close()
+
+
+def test_plan_levels_gives_a_converging_hierarchy(meshes):
+    """Sec. 4.1's coarsening heuristic on measured step times: the plan divides N,
+    and MGRIT with it reaches GPU sequential stepping."""
+    model = machine_model(pwm=PwmSpec(J0=1e6, f_carrier=20e3))
+    ctx, ids = make_ctx(meshes, model)
+    N, T = 4096, 20e-3
+    opts, est = ctx.mg_plan_levels(ids[2], ids[0], N, T, max_levels=5,
+                                   opts=api.mgrit_opts(tol=1e-4, max_iter=60))
+    assert est > 0.0
+    prod = 1
+    for l in range(opts.levels - 1):
+        assert opts.m[l] >= 2
+        prod *= opts.m[l]
+    assert N % prod == 0 and opts.space_level[0] == ids[2]
+    n = ctx.mg_num_dofs(ids[2])
+    a0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    seq = torch.empty((N + 1, n), dtype=torch.float64, device="cuda")
+    ctx.mg_sequential(ids[2], N, T, a0, seq)
+    out = torch.empty_like(seq)
+    rc, st = ctx.mg_solve(N, T, a0, out, opts, allow=(-7,))
+    assert rc == 0, st["res_hist"]
+    err = ((out[1:] - seq[1:]).norm(dim=1) / seq[1:].norm(dim=1)).max().item()
+    assert err <= 1e-5, err
+    print("plan", opts.levels, [opts.m[l] for l in range(opts.levels - 1)], "est ms/iter", est,
+          "iters", st["iters"], "solve s", st["t_solve"])
+    ctx.close()
