@@ -273,6 +273,11 @@ typedef struct {
                               maximal relative change of the Joule losses at C-points between
                               two iterations <= tol (Sec. 5.1); res_hist then holds that
                               change (the first entry infinite)                            */
+    double step_tol_ratio; /* > 0: inexact step solves (no counterpart in the paper): the steps of
+                              an iteration are solved to max(solver tolerance, step_tol_ratio x
+                              the current relative residual), so early iterations, whose iterate
+                              is still far from the solution, do not solve to full accuracy; the
+                              converged result is unchanged. 0 (default): fixed tolerance    */
 } mg_opts;
 
 /* Fill opts with defaults: 2 levels, m = 16, FCF, tol 1e-10 relative,

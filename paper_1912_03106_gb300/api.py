@@ -47,7 +47,7 @@ def solver_opts(**kw) -> L.mg_solver_opts:
 
 def mgrit_opts(levels=2, m=(16,), space_level=(0, 0), relax=1, tol=1e-10, tol_relative=True, max_iter=50,
                restrict_mode=2, solver: L.mg_solver_opts | None = None, cycle="V", nested=False,
-               stop="residual") -> L.mg_opts:
+               stop="residual", step_tol_ratio=0.0) -> L.mg_opts:
     lib = L.load()
     o = L.mg_opts()
     lib.mg_opts_defaults(C.byref(o))
@@ -64,6 +64,7 @@ def mgrit_opts(levels=2, m=(16,), space_level=(0, 0), relax=1, tol=1e-10, tol_re
     o.cycle = {"V": 0, "F": 1}[cycle]
     o.nested = 2 if nested == "reference" else int(bool(nested))
     o.stop_rule = {"residual": 0, "joule": 1}[stop]
+    o.step_tol_ratio = step_tol_ratio
     if solver is not None:
         o.solver = solver
     return o

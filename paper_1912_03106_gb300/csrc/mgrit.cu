@@ -562,7 +562,8 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
     check_solver_opts(o.solver);
     if (N <= 0 || !(T > 0.0) || !a0 || !out || o.levels < 1 || o.levels > 8 || o.relax < 0 || o.relax > 4 ||
         o.max_iter < 0 || !(o.tol >= 0.0) || o.restrict_mode < 0 || o.restrict_mode > 2 || o.cycle < 0 ||
-        o.cycle > 1 || o.nested < 0 || o.nested > 2 || o.stop_rule < 0 || o.stop_rule > 1)
+        o.cycle > 1 || o.nested < 0 || o.nested > 2 || o.stop_rule < 0 || o.stop_rule > 1 ||
+        !(o.step_tol_ratio >= 0.0))
         mg_fail(MG_EINVAL, "mg_solve: bad arguments");
     auto t0 = clk::now();
     ctx_finalize(c);
@@ -672,6 +673,15 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
     double r0 = 0.0;
     int it = 0;
     bool converged = false;
+    // inexact step solves: tolerance proportional to the current relative residual
+    const bool adaptive = o.step_tol_ratio > 0.0 && o.stop_rule == 0;
+    const double tol_cg = o.solver.cg_tol, tol_ref = o.solver.refine_tol;
+    auto set_step_tol = [&](double rho) {
+        if (!adaptive) return;
+        S.o.solver.cg_tol = std::max(tol_cg, o.step_tol_ratio * rho);
+        S.o.solver.refine_tol = std::max(tol_ref, o.step_tol_ratio * rho);
+    };
+    set_step_tol(1.0);
     for (it = 0;; ++it) {
         S.relax(0);
         S.residual(0);
@@ -687,6 +697,7 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
             break;
         }
         if (rn != rn || it >= o.max_iter) break;
+        set_step_tol(r0 > 0.0 ? rn / r0 : 1.0);
         S.coarse_correction(0, o.cycle);
     }
     k_to_time_major<<<nblk(L0.n * (N + 1)), 256, 0, c->stream>>>(L0.n, N, L0.view(), out);

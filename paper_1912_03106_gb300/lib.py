@@ -85,6 +85,7 @@ class mg_opts(C.Structure):
         ("cycle", C.c_int),
         ("nested", C.c_int),
         ("stop_rule", C.c_int),
+        ("step_tol_ratio", C.c_double),
     ]
 
 

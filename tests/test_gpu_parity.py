@@ -284,6 +284,18 @@ def test_nested_guess_alone_matches_oracle(meshes, lin5k):
     assert err <= 1e-10, err
 
 
+def test_inexact_step_solves_reach_the_same_solution(meshes, lin5k):
+    """step_tol_ratio > 0 solves the steps of early iterations loosely; the
+    iteration still converges to the sequential solution (tight final stop)."""
+    model, ctx, ids = lin5k
+    N, T = 256, 5e-3
+    ref = MachineProblem(meshes, model, N, T, (1,), ()).sequential()
+    opts = api.mgrit_opts(levels=3, m=(8, 4), space_level=(ids[1], ids[0], ids[0]), relax=1, tol=1e-9,
+                          max_iter=80, step_tol_ratio=1e-3)
+    got, st = run_mgrit(ctx, N, T, ref.shape[1], opts)
+    assert rel_err_per_point(got, ref).max() <= 1e-9
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_mgrit_on_the_graph_path(meshes, lin5k, precision):
     """64 intervals per batched step: the fine level runs on the graph path."""
