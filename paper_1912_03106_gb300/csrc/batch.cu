@@ -45,6 +45,22 @@ constexpr int NTB = 256;  // threads per block
 #ifndef MG_RBS1
 #define MG_RBS1 64
 #endif
+// Programmatic dependent launch between consecutive phase kernels (MG_PDL = 1):
+// each kernel waits for its predecessor's completion (griddepcontrol.wait) before
+// touching its outputs and lets its own successor be scheduled as soon as all of
+// its blocks run (griddepcontrol.launch_dependents).  Measured on GB300 it slows
+// the 18,240 x 256 step (12.2 against 11.4 ms): the early successor blocks take
+// resources from the running phase.  Off by default.
+#ifndef MG_PDL
+#define MG_PDL 0
+#endif
+__device__ __forceinline__ void phase_begin() {
+#if MG_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
 // minimum resident blocks per SM for the FP32 multigrid kernels (caps registers)
 #ifndef MG_MINB_F
 #define MG_MINB_F 5
@@ -126,16 +142,6 @@ __device__ __forceinline__ double col_total(const double* part, int nrb, int gc)
     return s;
 }
 
-// Column totals with TPC threads per column (TPC a power of two <= 32, consecutive
-// lanes): each thread adds every TPC-th row block, then a fixed shuffle tree.
-// All TPC threads of a column return the total.
-__device__ __forceinline__ double col_total_par(const double* part, int nrb, int gc, int tpc, int sub) {
-    const int t = gc / G, l = gc % G;
-    double s = 0.0;
-    for (int rb = sub; rb < nrb; rb += tpc) s += part[((size_t)t * nrb + rb) * G + l];
-    for (int off = 1; off < tpc; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    return s;
-}
 
 template <class T>
 __device__ __forceinline__ T* tv(T* base, int n, int t) { return base + (size_t)t * n * G; }
@@ -147,6 +153,7 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
                                                const double* __restrict__ F, double J0, double* x64, double* r64,
                                                double* p64, double* q64, double* b64, float* z, double* part_bb,
                                                double* part_rr, float* r32s) {
+    phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
@@ -204,6 +211,7 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
 
 // x_out = x + g
 __global__ void __launch_bounds__(NTB) kb_final(Depth D, const CallArgs* __restrict__ ca, const double* x64) {
+    phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
@@ -223,6 +231,7 @@ constexpr int NSB = 1024;
 __global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* part_bb, const double* part_rr, int nrb,
                                                       int kpad, const CallArgs* __restrict__ ca,
                                                       cudaGraphConditionalHandle h, int use_cond) {
+    phase_begin();
     int any = 0;
     for (int c = threadIdx.x; c < kpad; c += NSB) {
         const double bb = col_total(part_bb, nrb, c), rr = col_total(part_rr, nrb, c);
@@ -247,6 +256,7 @@ __global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* pa
 __global__ void __launch_bounds__(NSB) kb_scalar_init1(Cols st, const double* part_bb, int nrb, int kpad,
                                                       const CallArgs* __restrict__ ca, cudaGraphConditionalHandle h,
                                                       int use_cond) {
+    phase_begin();
     for (int c = threadIdx.x; c < kpad; c += NSB) {
         st.bb[c] = col_total(part_bb, nrb, c);
         st.outer[c] = c < ca->k;
@@ -276,6 +286,7 @@ __device__ __forceinline__ void tile_totals(const double* part, int nrb, int t, 
 
 // (r, z) -> gamma, beta
 __global__ void __launch_bounds__(NTB) kb_scalar_gamma(Cols st, const double* part, int nrb) {
+    phase_begin();
     __shared__ double rz[G];
     tile_totals(part, nrb, blockIdx.x, rz);
     if (threadIdx.x < G) {
@@ -288,6 +299,7 @@ __global__ void __launch_bounds__(NTB) kb_scalar_gamma(Cols st, const double* pa
 
 // (p, q) -> alpha
 __global__ void __launch_bounds__(NTB) kb_scalar_alpha(Cols st, const double* part, int nrb) {
+    phase_begin();
     __shared__ double pq[G];
     tile_totals(part, nrb, blockIdx.x, pq);
     if (threadIdx.x < G) {
@@ -303,6 +315,7 @@ __global__ void __launch_bounds__(NTB) kb_scalar_alpha(Cols st, const double* pa
 __global__ void __launch_bounds__(NTB) kb_scalar_conv(Cols st, const double* part, int nrb,
                                                      const CallArgs* __restrict__ ca, int inner,
                                                      cudaGraphConditionalHandle h, int use_cond) {
+    phase_begin();
     const double tol2 = inner ? ca->inner_tol2 : ca->tol2;
     __shared__ double rr[G];
     tile_totals(part, nrb, blockIdx.x, rr);
@@ -337,6 +350,7 @@ __global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* p
                                                        const CallArgs* __restrict__ ca,
                                                        cudaGraphConditionalHandle h_inner,
                                                        cudaGraphConditionalHandle h_outer, int use_cond) {
+    phase_begin();
     const int sweep = st.ctr[1];
     int any = 0;
     for (int c = threadIdx.x; c < kpad; c += NSB) {
@@ -368,6 +382,7 @@ __global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* p
 // statuses and iteration totals into the context counters
 __global__ void __launch_bounds__(NSB) kb_scalar_final(Cols st, int kpad, const CallArgs* __restrict__ ca, int mode,
                                                       unsigned long long* iter_sum, int* worst) {
+    phase_begin();
     for (int c = threadIdx.x; c < kpad && c < ca->k; c += NSB) {
         const int failed = mode == 0 ? st.act[c] : st.outer[c] != 0;
         if (failed) atomicMin(worst, (int)MG_ECG_MAXIT);
@@ -463,6 +478,7 @@ constexpr int RPPF = NTB / TPRF;   // rows per pass
 // x = w D^-1 r, s = r - w (L D^-1) r
 template <class RT, bool PC>
 __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth_first(Depth D, const RT* rin_base, float w) {
+    phase_begin();
     ROWS_F(D, t, rb, i) {
         const RT* rin = tv(rin_base, D.n, t);
         RT rv[VF];
@@ -487,6 +503,7 @@ __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth_first(Depth D, const
 template <class RT, bool PC>
 __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth(Depth D, const float* src_base, float* dst_base, const RT* rtop_base,
                                                  float w, double* part) {
+    phase_begin();
     double rz[VF] = {0.0, 0.0, 0.0, 0.0};
     {
         ROWS_F(D, t, rb, i) {
@@ -522,6 +539,7 @@ __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth(Depth D, const float
 
 // r_c = P^T s over the coarse rows (grid over the coarse depth's row blocks)
 __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_restrict(Depth D, Depth C, const float* src_base) {
+    phase_begin();
     ROWS_F(C, t, rb, ic) {
         const float* src = tv(src_base, D.n, t);
         float acc[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -539,6 +557,7 @@ __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_restrict(Depth D, Depth C, 
 
 // y = P x_c, x += y  (x_c = sum of `parts` partial vectors pstride apart)
 __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_prolong(Depth D, Depth C, int parts, size_t pstride) {
+    phase_begin();
     ROWS_F(D, t, rb, i) {
         const float* xc = tv(C.x, C.n, t);
         float yv[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -572,6 +591,7 @@ __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_prolong(Depth D, Depth C, i
 // s -= L y
 template <bool PC>
 __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_resupdate(Depth D, float* s_base) {
+    phase_begin();
     ROWS_F(D, t, rb, i) {
         float* s = tv(s_base, D.n, t);
         float acc[VF], sv[VF];
@@ -619,6 +639,7 @@ constexpr int BASE_KSPLIT = 4;  // K splits of the dense base solve (partials su
 template <class RT, int TB, int BKT>
 __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __restrict__ A, const RT* r_base,
                                                      float* x_base, int ntile, int ks, size_t pstride) {
+    phase_begin();
     __shared__ __align__(16) float As[64][BKT + 4];    // +4: conflict-free fragment reads
     __shared__ __align__(16) float Bs[BKT][TB * G + 8];  // +8: conflict-free fragment reads
     const int nrb = (n0 + 63) / 64;
@@ -681,6 +702,26 @@ __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __rest
     }
 }
 
+// launch with the programmatic-dependent-launch attribute (see phase_begin)
+template <typename... KArgs, typename... Args>
+void pdl_launch(void (*kern)(KArgs...), unsigned g, unsigned b, size_t smem, cudaStream_t s, Args... args) {
+#if MG_PDL
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g);
+    cfg.blockDim = dim3(b);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    MG_CUDA(cudaLaunchKernelEx(&cfg, kern, (KArgs)args...));
+#else
+    kern<<<g, b, smem, s>>>((KArgs)args...);
+#endif
+}
+
 // launch the dense base solve with TB tiles per block for ntile tiles
 #ifndef MG_BASE_TB
 #define MG_BASE_TB 2
@@ -692,19 +733,20 @@ void launch_base_dense(cudaStream_t s, int n0, const float* A, const RT* r, floa
     if (tb <= 0) tb = ks > 1 ? MG_BASE_TB : 1;  // library choice
     if (tb >= 4 && ntile >= 4) {
         const unsigned nb = (unsigned)(nrb * ((ntile + 3) / 4) * ks);
-        kb_base_dense<RT, 4, 64><<<nb, 128, 0, s>>>(n0, A, r, x, ntile, ks, pstride);
+        pdl_launch(kb_base_dense<RT, 4, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
     } else if (tb >= 2 && ntile >= 2) {
         const unsigned nb = (unsigned)(nrb * ((ntile + 1) / 2) * ks);
-        kb_base_dense<RT, 2, 64><<<nb, 128, 0, s>>>(n0, A, r, x, ntile, ks, pstride);
+        pdl_launch(kb_base_dense<RT, 2, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
     } else {
         const unsigned nb = (unsigned)(nrb * ntile * ks);
-        kb_base_dense<RT, 1, 128><<<nb, 128, 0, s>>>(n0, A, r, x, ntile, ks, pstride);
+        pdl_launch(kb_base_dense<RT, 1, 128>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
     }
 }
 
 // coarsest level without a dense inverse, or Jacobi preconditioning: x = w D^-1 r
 template <class RT, bool PC>
 __global__ void __launch_bounds__(NTB) kb_jacobi(Depth D, const RT* r_base, float w, double* part) {
+    phase_begin();
     double rz[VF] = {0.0, 0.0, 0.0, 0.0};
     {
         ROWS_F(D, t, rb, i) {
@@ -738,6 +780,7 @@ template <class RT>
 __global__ void __launch_bounds__(32 * BAND_WARPS) kb_base_band(int n, int u, int stride, const float* __restrict__ Lb,
                                                               const float* __restrict__ Ub, const RT* r_base,
                                                               float* x_base) {
+    phase_begin();
     extern __shared__ float4 band_sm4[];
     float* band_sm = reinterpret_cast<float*>(band_sm4);
     __shared__ float ring_sm[BAND_WARPS][BAND_RING];
@@ -790,6 +833,7 @@ __global__ void __launch_bounds__(32 * BAND_WARPS) kb_base_band(int n, int u, in
 __global__ void __launch_bounds__(NTB) kb_init_pc(Depth D, const double* __restrict__ R, const int* __restrict__ state,
                                                   double* x64, double* r64, double* p64, double* q64, float* z,
                                                   double* part_bb, double* part_rr, float* r32s) {
+    phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
@@ -823,6 +867,7 @@ struct VecOf {
 template <class T, bool PC>
 __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base, T* q_base, const double* beta,
                                                 double* part) {
+    phase_begin();
     constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
     int t, rb;
     tile_rb(D.nrb, t, rb);
@@ -858,6 +903,7 @@ __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base,
 template <class T>
 __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, const T* p_base, const T* q_base,
                                                 const double* alpha, double* part, float* r32_base) {
+    phase_begin();
     constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
     int t, rb;
     tile_rb(D.nrb, t, rb);
@@ -899,6 +945,7 @@ __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, c
 __global__ void __launch_bounds__(NTB) kb_refine_r(Depth D, const double* b64, const double* x64, float* r32,
                                                    float* d32, float* p32, float* q32, const int* outer,
                                                    double* part) {
+    phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
@@ -924,6 +971,7 @@ __global__ void __launch_bounds__(NTB) kb_refine_r(Depth D, const double* b64, c
 }
 
 __global__ void __launch_bounds__(NTB) kb_update_x(Depth D, double* x64, const float* d32, const int* outer) {
+    phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
@@ -976,6 +1024,7 @@ void* alloc(GraphPlan& P, size_t bytes) {
 
 inline unsigned grid(int ntile, int nrb) { return (unsigned)(ntile * nrb); }
 
+
 // one preconditioner application on the capture stream: z = B r into depth[0].x;
 // the last kernel writes the (r, z) partials into part.  PC: per-column operators
 // at every depth and a per-column banded Cholesky factor on the base depth.
@@ -985,23 +1034,23 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
     const float w = P.omega;
     if (P.precond == 0) {
         Depth& D = P.depth[0];
-        kb_jacobi<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, rtop, 1.0f, part);
+        pdl_launch(kb_jacobi<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, 1.0f, part);
         return;
     }
     std::vector<int> sel(nd, 0);
     for (int d = 0; d < nd - 1; ++d) {
         Depth& D = P.depth[d];
-        if (d == 0) kb_smooth_first<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, rtop, w);
-        else kb_smooth_first<float, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, D.r, w);
+        if (d == 0) pdl_launch(kb_smooth_first<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, w);
+        else pdl_launch(kb_smooth_first<float, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.r, w);
         int sl = 0;
         for (int sw = 1; sw < P.nu; ++sw) {
-            kb_smooth<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr, w,
+            pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr, w,
                                                                   nullptr);
             sl ^= 1;
         }
         sel[d] = sl;
         Depth& C = P.depth[d + 1];
-        kb_restrict<<<grid(P.ntile, C.nrb), NTB, 0, s>>>(D, C, sl ? D.sb : D.sa);
+        pdl_launch(kb_restrict, grid(P.ntile, C.nrb), NTB, 0, s, D, C, sl ? D.sb : D.sa);
     }
     Depth& B = P.depth[nd - 1];
     const size_t pstride = (size_t)P.ntile * B.n * G;
@@ -1010,9 +1059,9 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
     if (PC) {
         const unsigned nb = (unsigned)(P.ntile * G / BAND_WARPS);
         const size_t smem = (size_t)BAND_WARPS * BAND_CHUNK * P.pco.band_stride * sizeof(float);
-        if (nd == 1) kb_base_band<RT><<<nb, 32 * BAND_WARPS, smem, s>>>(B.n, P.pco.band_u, P.pco.band_stride,
+        if (nd == 1) pdl_launch(kb_base_band<RT>, nb, 32 * BAND_WARPS, smem, s, B.n, P.pco.band_u, P.pco.band_stride,
                                                                        P.pco.band_L, P.pco.band_U, rtop, B.x);
-        else kb_base_band<float><<<nb, 32 * BAND_WARPS, smem, s>>>(B.n, P.pco.band_u, P.pco.band_stride,
+        else pdl_launch(kb_base_band<float>, nb, 32 * BAND_WARPS, smem, s, B.n, P.pco.band_u, P.pco.band_stride,
                                                                   P.pco.band_L, P.pco.band_U, B.r, B.x);
     } else if (P.op->base_inv.p) {
         if (nd == 1) launch_base_dense<RT>(s, B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0, P.base_tb);
@@ -1020,26 +1069,26 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
                                       P.base_tb);
         parts = ks;
     } else {
-        if (nd == 1) kb_jacobi<RT, PC><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, rtop, w, nullptr);
-        else kb_jacobi<float, PC><<<grid(P.ntile, B.nrb), NTB, 0, s>>>(B, B.r, w, nullptr);
+        if (nd == 1) pdl_launch(kb_jacobi<RT, PC>, grid(P.ntile, B.nrb), NTB, 0, s, B, rtop, w, nullptr);
+        else pdl_launch(kb_jacobi<float, PC>, grid(P.ntile, B.nrb), NTB, 0, s, B, B.r, w, nullptr);
     }
     if (nd == 1) {
         // z is final; a zero-weight sweep accumulates (r, z) for a single-level hierarchy
         Depth& D = P.depth[0];
-        kb_smooth<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, D.x, nullptr, rtop, 0.0f, part);
+        pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.x, nullptr, rtop, 0.0f, part);
         return;
     }
     for (int d = nd - 2; d >= 0; --d) {
         Depth& D = P.depth[d];
         Depth& C = P.depth[d + 1];
         const bool from_base = d + 1 == nd - 1;
-        kb_prolong<<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, C, from_base ? parts : 1, pstride);
+        pdl_launch(kb_prolong, grid(P.ntile, D.nrb), NTB, 0, s, D, C, from_base ? parts : 1, pstride);
         int sl = sel[d];
-        kb_resupdate<PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa);
+        pdl_launch(kb_resupdate<PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa);
         for (int sw = 0; sw < P.nu; ++sw) {
             const bool last = sw == P.nu - 1;
             const bool top = last && d == 0;
-            kb_smooth<RT, PC><<<grid(P.ntile, D.nrb), NTB, 0, s>>>(D, sl ? D.sb : D.sa,
+            pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa,
                                                                   last ? nullptr : (sl ? D.sa : D.sb),
                                                                   top ? rtop : nullptr, w, top ? part : nullptr);
             sl ^= 1;
@@ -1064,13 +1113,13 @@ void capture_pcg_body(GraphPlan& P, cudaStream_t s, T* d, T* r, T* p, T* q, cons
     if constexpr (std::is_same<T, double>::value) rf = P.r32s;
     else rf = r;
     capture_precondition<float>(P, s, rf, part);
-    kb_scalar_gamma<<<P.ntile, NTB, 0, s>>>(P.st, part, D0.nrb);
-    if (P.pc) kb_pcg_a<T, true><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
-    else kb_pcg_a<T, false><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, Lv, p, q, P.st.beta, part);
-    kb_scalar_alpha<<<P.ntile, NTB, 0, s>>>(P.st, part, D0.nrb);
-    kb_pcg_b<T><<<grid(P.ntile, D0.nrb), NTB, 0, s>>>(D0, d, r, p, q, P.st.alpha, part,
+    pdl_launch(kb_scalar_gamma, P.ntile, NTB, 0, s, P.st, part, D0.nrb);
+    if (P.pc) pdl_launch(kb_pcg_a<T, true>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, Lv, p, q, P.st.beta, part);
+    else pdl_launch(kb_pcg_a<T, false>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, Lv, p, q, P.st.beta, part);
+    pdl_launch(kb_scalar_alpha, P.ntile, NTB, 0, s, P.st, part, D0.nrb);
+    pdl_launch(kb_pcg_b<T>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, d, r, p, q, P.st.alpha, part,
                                                        std::is_same<T, double>::value ? P.r32s : nullptr);
-    kb_scalar_conv<<<P.ntile, NTB, 0, s>>>(P.st, part, D0.nrb, ca, inner, h, use_cond);
+    pdl_launch(kb_scalar_conv, P.ntile, NTB, 0, s, P.st, part, D0.nrb, ca, inner, h, use_cond);
 }
 
 // append a WHILE node at the capture's current position; returns its body graph
