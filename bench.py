@@ -44,7 +44,7 @@ ERR_TARGET = 1e-6   # metric: maximal relative L2 error per time point vs sequen
 ERR_MARGIN = 0.5    # calibrate to half the target
 TOL_LADDER = (1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7, 1e-8)
 # MGRIT solves the steps of iteration k to max(1e-13, STEP_TOL_RATIO x relative residual)
-STEP_TOL_RATIO = 1e-3
+STEP_TOL_RATIO = 3e-4
 # step-solve tolerances tried for the sequential baseline, loosest first
 SEQ_TOL_LADDER = (1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 1e-11, 1e-13)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
