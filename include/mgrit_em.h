@@ -128,6 +128,17 @@ typedef enum { MG_FP64 = 0, MG_FP32_REFINE = 1 } mg_precision;
 
 typedef enum { MG_PRECOND_JACOBI = 0, MG_PRECOND_MULTIGRID = 1 } mg_precond;
 
+/* Smoother of the multigrid V-cycle.  Both are polynomial (Richardson) sweeps
+ * x += w_s D^-1 (r - L x) with the Jacobi diagonal D.  MG_SMOOTH_JACOBI: every
+ * sweep has the weight omega.  MG_SMOOTH_CHEBYSHEV: the nu sweeps of a pre- (and,
+ * in reverse order, post-) smoothing take as weights the reciprocals of the nu
+ * roots of the first-kind Chebyshev polynomial on [lam / cheb_ratio, lam], lam
+ * the Gershgorin bound max_i sum_j |L_ij| / L_ii of the depth's operator, so that
+ * the sweeps together damp that whole upper part of the spectrum of D^-1 L (the
+ * factors commute, so the V-cycle stays symmetric).  Steps of nonlinear meshes
+ * (per-column Jacobians) always use damped Jacobi. */
+typedef enum { MG_SMOOTH_CHEBYSHEV = 0, MG_SMOOTH_JACOBI = 1 } mg_smoother;
+
 /* How a batched step runs: MG_PATH_CLUSTER = one persistent launch, a thread-block
  * cluster per tile of columns (lowest latency for few columns); MG_PATH_GRAPH =
  * one kernel per phase over all columns, the iteration loop inside a CUDA graph
@@ -150,8 +161,9 @@ typedef struct {
                            choice (16 for a single column tile when the device allows it, else 8) */
     int tile;           /* columns per cluster (1, 8, 16, 32), 0 = library choice          */
     int precond;        /* mg_precond                                                      */
-    int smooth;         /* damped-Jacobi sweeps before and after each coarse correction    */
-    double omega;       /* Jacobi damping factor                                           */
+    int smooth;         /* smoothing sweeps before and after each coarse correction (1..8),
+                           0 = library choice (5)                                          */
+    double omega;       /* MG_SMOOTH_JACOBI weight (and of Newton steps' smoothing)        */
     int path;           /* mg_path                                                         */
     /* nonlinear steps (meshes with a Brauer-law material, Sec. 5): damped Newton,
      * each correction J delta = -F solved by the PCG above (FP64 form, multigrid
@@ -167,12 +179,16 @@ typedef struct {
     int rows_per_block;        /* rows per block on the finest multigrid depth (16..4096)   */
     int coarse_rows_per_block; /* rows per block on the coarser depths (16..4096)           */
     int base_tiles;            /* 16-column tiles per block of the dense base solve (1, 2, 4) */
+    int smoother;              /* mg_smoother                                               */
+    double cheb_ratio;         /* MG_SMOOTH_CHEBYSHEV: lam over the lower end of the damped
+                                  interval (1 < cheb_ratio <= 1e4), 0 = library choice (30) */
 } mg_solver_opts;
 
 /* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,
- * inner_tol 1e-5, max_cg 2000, max_refine 30, FP64, multigrid with 2 sweeps
- * of damping 0.7; newton_tol 1e-8, max_newton 100, max_halvings 40,
- * newton_lin_tol 1e-6). */
+ * inner_tol 1e-5, max_cg 2000, max_refine 30, FP64, multigrid with 5 Chebyshev
+ * sweeps on [lam/30, lam] before and after each coarse correction (Newton steps:
+ * 5 damped-Jacobi sweeps of weight 0.7); newton_tol 1e-8, max_newton 100,
+ * max_halvings 40, newton_lin_tol 1e-6). */
 void mg_solver_defaults(mg_solver_opts* opts);
 
 typedef struct {

@@ -993,6 +993,9 @@ struct GraphPlan {
     int rbs0 = 0, rbs1 = 0, base_tb = 0;  // launch shape (0: library choice)
     PcOperator pco{};
     float omega = 0.7f;
+    int smoother = 0;
+    double cheb_ratio = 0.0;
+    float wsm[MG_MAX_DEPTH][MG_MAX_NU] = {};  // sweep weights of each depth's pre-smoothing
     std::vector<DBuf> bufs;
     DBuf args, cols, part;
     std::vector<Depth> depth;
@@ -1031,7 +1034,7 @@ inline unsigned grid(int ntile, int nrb) { return (unsigned)(ntile * nrb); }
 template <class RT, bool PC>
 void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double* part) {
     const int nd = (int)P.depth.size();
-    const float w = P.omega;
+    const float w = P.omega;  // base-depth Jacobi sweep without a dense inverse
     if (P.precond == 0) {
         Depth& D = P.depth[0];
         pdl_launch(kb_jacobi<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, 1.0f, part);
@@ -1040,12 +1043,13 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
     std::vector<int> sel(nd, 0);
     for (int d = 0; d < nd - 1; ++d) {
         Depth& D = P.depth[d];
-        if (d == 0) pdl_launch(kb_smooth_first<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, w);
-        else pdl_launch(kb_smooth_first<float, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.r, w);
+        const float* ws = P.wsm[d];
+        if (d == 0) pdl_launch(kb_smooth_first<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, ws[0]);
+        else pdl_launch(kb_smooth_first<float, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.r, ws[0]);
         int sl = 0;
         for (int sw = 1; sw < P.nu; ++sw) {
-            pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr, w,
-                                                                  nullptr);
+            pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr,
+                       ws[sw], nullptr);
             sl ^= 1;
         }
         sel[d] = sl;
@@ -1089,8 +1093,8 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
             const bool last = sw == P.nu - 1;
             const bool top = last && d == 0;
             pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa,
-                                                                  last ? nullptr : (sl ? D.sa : D.sb),
-                                                                  top ? rtop : nullptr, w, top ? part : nullptr);
+                       last ? nullptr : (sl ? D.sa : D.sb), top ? rtop : nullptr, P.wsm[d][P.nu - 1 - sw],
+                       top ? part : nullptr);
             sl ^= 1;
         }
     }
@@ -1164,8 +1168,12 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         }
         P->precision = so.precision;
         P->precond = so.precond;
-        P->nu = so.smooth > 0 ? so.smooth : 2;
+        P->nu = smooth_sweeps(so);
         P->omega = so.omega > 0.0 ? (float)so.omega : 0.7f;
+        P->smoother = so.smoother;
+        P->cheb_ratio = so.cheb_ratio;
+        for (int d = 0; d < (int)op.mg.size() && d < MG_MAX_DEPTH; ++d)
+            smoother_weights(*op.mg[d], so, P->pc, P->nu, P->wsm[d]);
         const MeshLevel& m0 = c->meshes[op.mesh];
         const int nd = so.precond == MG_PRECOND_MULTIGRID ? (int)op.mg.size() : 1;
         for (int d = 0; d < nd; ++d) {
@@ -1339,7 +1347,8 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
     GraphPlan* P = nullptr;
     for (auto* q : c->plans)
         if (!q->pc && q->op == &op && q->ntile == ntile && q->precision == so.precision && q->precond == so.precond &&
-            q->nu == (so.smooth > 0 ? so.smooth : 2) && q->omega == (so.omega > 0.0 ? (float)so.omega : 0.7f) &&
+            q->nu == smooth_sweeps(so) && q->omega == (so.omega > 0.0 ? (float)so.omega : 0.7f) &&
+            q->smoother == so.smoother && q->cheb_ratio == so.cheb_ratio &&
             q->rbs0 == so.rows_per_block && q->rbs1 == so.coarse_rows_per_block && q->base_tb == so.base_tiles) {
             P = q;
             break;

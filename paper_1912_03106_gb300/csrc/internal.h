@@ -14,6 +14,7 @@
 #define MG_MAX_REGIONS 64
 #define MG_MAX_DEPTH 6
 #define MG_MAX_DENSE 4096   // largest base mesh inverted densely
+#define MG_MAX_NU 8         // smoothing sweeps per side of the V-cycle
 
 struct MgError {
     mg_status st;
@@ -103,6 +104,7 @@ struct MgDepth {
     int64_t n = 0;
     int W = 0;
     DBuf L64, M64, L32, LD32, dinv64, dinv32;  // ELL values (W x n) and Jacobi data
+    float lam = 0.0f;  // Gershgorin bound of the spectrum of D^-1 L (rounded up)
 };
 
 // L = M / dt + K on one mesh level and its multigrid hierarchy: depth 0 is the
@@ -180,6 +182,10 @@ const int8_t* ctx_pwm_table(mg_ctx* c, int64_t N, double T);
 const double* ctx_wave_table(mg_ctx* c, int64_t N, double T, int kind);
 // Lookups that never allocate: null if the operator / PWM table was not built yet.
 const StepOp* ctx_find_step_op(const mg_ctx* c, int mesh, double dt);
+// Weights of the nu smoothing sweeps of one pre-smoothing on depth d (post-smoothing
+// takes them in reverse order): Chebyshev roots on [lam / ratio, lam] or omega.
+void smoother_weights(const MgDepth& d, const mg_solver_opts& so, bool per_column, int nu, float* w);
+inline int smooth_sweeps(const mg_solver_opts& so) { return so.smooth > 0 ? so.smooth : 5; }
 const int8_t* ctx_find_pwm_table(const mg_ctx* c, int64_t N, double T);
 const double* ctx_find_wave_table(const mg_ctx* c, int64_t N, double T, int kind);
 

@@ -474,11 +474,13 @@ void check_solver_opts(const mg_solver_opts& so) {
     if (so.max_cg < 1 || so.max_refine < 0 || !(so.cg_tol >= 0.0) || !(so.refine_tol >= 0.0) ||
         !(so.inner_tol >= 0.0) || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) || so.cluster < 0 ||
         so.cluster > 16 || !(so.tile == 0 || so.tile == 1 || so.tile == 8 || so.tile == 16 || so.tile == 32) ||
-        (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID) || so.smooth < 0 || so.smooth > 8 ||
+        (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID) || so.smooth < 0 || so.smooth > MG_MAX_NU ||
         !(so.omega >= 0.0 && so.omega < 2.0) || so.path < MG_PATH_AUTO || so.path > MG_PATH_GRAPH ||
         !(so.rows_per_block == 0 || (so.rows_per_block >= 16 && so.rows_per_block <= 4096)) ||
         !(so.coarse_rows_per_block == 0 || (so.coarse_rows_per_block >= 16 && so.coarse_rows_per_block <= 4096)) ||
-        !(so.base_tiles == 0 || so.base_tiles == 1 || so.base_tiles == 2 || so.base_tiles == 4))
+        !(so.base_tiles == 0 || so.base_tiles == 1 || so.base_tiles == 2 || so.base_tiles == 4) ||
+        (so.smoother != MG_SMOOTH_CHEBYSHEV && so.smoother != MG_SMOOTH_JACOBI) ||
+        !(so.cheb_ratio == 0.0 || (so.cheb_ratio > 1.0 && so.cheb_ratio <= 1e4)))
         mg_fail(MG_EINVAL, "bad solver options");
 }
 
@@ -746,12 +748,14 @@ void mg_solver_defaults(mg_solver_opts* s) {
     s->cluster = 0;
     s->tile = 0;
     s->precond = MG_PRECOND_MULTIGRID;
-    s->smooth = 2;
+    s->smooth = 5;
     s->omega = 0.7;
     s->newton_tol = 1e-8;
     s->max_newton = 100;
     s->max_halvings = 40;
     s->newton_lin_tol = 1e-6;
+    s->smoother = MG_SMOOTH_CHEBYSHEV;
+    s->cheb_ratio = 30.0;
 }
 
 void mg_opts_defaults(mg_opts* o) {

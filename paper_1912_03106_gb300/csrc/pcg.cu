@@ -90,7 +90,8 @@ struct PcgArgs {
     const float* base_inv;  // dense inverse on the deepest level (or null)
     int precond;            // 0 Jacobi, 1 multigrid V-cycle
     int nu;                 // smoothing sweeps before and after the coarse correction
-    float omega;            // Jacobi damping
+    float omega;            // Jacobi weight of the base-depth sweep without a dense inverse
+    float wsm[MG_MAX_DEPTH][MG_MAX_NU];  // sweep weights of each depth's pre-smoothing
     double inv_dt;
     const double* F;  // 3 x n (depth 0)
     double J0;
@@ -470,6 +471,7 @@ __device__ void precondition(Ctx<KT>& c, const PcgArgs& a, const RT* rtop, float
     constexpr int V = vf(KT);
     const float w = a.omega;
     const int c0 = Lanes<KT, V>::c0();
+    const int nu = min(a.nu, MG_MAX_NU);
     if (a.precond == 0) {
         const DepthArgs& D = a.d[0];
         PhJacobi<KT, V, RT> ph{D, rtop, c.tv(D.x, D.n), c0, {}, {}, {}};
@@ -485,17 +487,18 @@ __device__ void precondition(Ctx<KT>& c, const PcgArgs& a, const RT* rtop, float
         float* x = c.tv(D.x, D.n);
         float* sa = c.tv(D.sa, D.n);
         float* sb = c.tv(D.sb, D.n);
+        const float* ws = a.wsm[dd];
         if (dd == 0) {
-            PhSmoothFirst<KT, V, RT> ph{D, rtop, x, sa, w, c0, {}, {}, {}};
+            PhSmoothFirst<KT, V, RT> ph{D, rtop, x, sa, ws[0], c0, {}, {}, {}};
             run_rows<KT, V>(c, D.n, ph);
         } else {
-            PhSmoothFirst<KT, V, float> ph{D, c.tv(D.r, D.n), x, sa, w, c0, {}, {}, {}};
+            PhSmoothFirst<KT, V, float> ph{D, c.tv(D.r, D.n), x, sa, ws[0], c0, {}, {}, {}};
             run_rows<KT, V>(c, D.n, ph);
         }
         c.cl.sync();
         int sl = 0;
-        for (int sw = 1; sw < a.nu; ++sw) {
-            PhSmooth<KT, V, RT> ph{D, sl ? sb : sa, sl ? sa : sb, x, nullptr, w, c0, false, {}, {}, {}, {}, {}, {}};
+        for (int sw = 1; sw < nu; ++sw) {
+            PhSmooth<KT, V, RT> ph{D, sl ? sb : sa, sl ? sa : sb, x, nullptr, ws[sw], c0, false, {}, {}, {}, {}, {}, {}};
             run_rows<KT, V>(c, D.n, ph);
             c.cl.sync();
             sl ^= 1;
@@ -557,10 +560,10 @@ __device__ void precondition(Ctx<KT>& c, const PcgArgs& a, const RT* rtop, float
             run_rows<KT, V>(c, D.n, ph);
         }
         c.cl.sync();
-        for (int sw = 0; sw < a.nu; ++sw) {
-            const bool last = sw == a.nu - 1;
-            PhSmooth<KT, V, RT> ph{D, sl ? sb : sa, sl ? sa : sb, x, (last && dd == 0) ? rtop : nullptr, w, c0, last,
-                                   {}, {}, {}, {}, {}, {}};
+        for (int sw = 0; sw < nu; ++sw) {
+            const bool last = sw == nu - 1;
+            PhSmooth<KT, V, RT> ph{D, sl ? sb : sa, sl ? sa : sb, x, (last && dd == 0) ? rtop : nullptr,
+                                   a.wsm[dd][nu - 1 - sw], c0, last, {}, {}, {}, {}, {}, {}};
             run_rows<KT, V>(c, D.n, ph);
             if (last && dd == 0) {
 #pragma unroll
@@ -973,9 +976,10 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
     csize = std::max(1, std::min(16, csize));
     PcgArgs a = {};
     a.precond = so.precond;
-    a.nu = so.smooth > 0 ? so.smooth : 2;
+    a.nu = smooth_sweeps(so);
     a.omega = so.omega > 0.0 ? (float)so.omega : 0.7f;
     a.nd = a.precond == 1 ? (int)op.mg.size() : 1;
+    for (int d = 0; d < a.nd; ++d) smoother_weights(*op.mg[d], so, false, a.nu, a.wsm[d]);
     a.base_inv = (a.precond == 1 && op.base_inv.p) ? op.base_inv.as<float>() : nullptr;
     // work vectors: each is ntile * n_d * KT elements
     int wsi = 0;
@@ -1146,9 +1150,10 @@ void static_step(void* arg) {
     const int ntile = (q.k + KT - 1) / KT;
     PcgArgs a = {};
     a.precond = so.precond;
-    a.nu = so.smooth > 0 ? so.smooth : 2;
+    a.nu = smooth_sweeps(so);
     a.omega = so.omega > 0.0 ? (float)so.omega : 0.7f;
     a.nd = a.precond == 1 ? (int)op->mg.size() : 1;
+    for (int d = 0; d < a.nd; ++d) smoother_weights(*op->mg[d], so, false, a.nu, a.wsm[d]);
     a.base_inv = (a.precond == 1 && op->base_inv.p) ? op->base_inv.as<float>() : nullptr;
     // carve the work vectors out of the static array (256-byte aligned pieces)
     const size_t e0 = (size_t)ntile * m0.n * KT;

@@ -197,6 +197,18 @@ __global__ void k_ell_scaled(int64_t nW, int64_t n, const int32_t* __restrict__ 
     LD32[q] = (float)(L64[q] * dinv64[col[q]]);
 }
 
+// Gershgorin bound of the spectrum of D^-1 L: max over rows of sum_j |L_ij| / L_ii,
+// rounded up to float; a positive float's bits order like the value, so the
+// maximum is an unsigned atomicMax.
+__global__ void k_ell_gershgorin(int64_t n, int W, const double* __restrict__ L64, const double* __restrict__ dinv64,
+                                 unsigned* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = 0.0;
+    for (int w = 0; w < W; ++w) a += fabs(L64[w * n + i]);
+    atomicMax(out, __float_as_uint(__double2float_ru(a * dinv64[i])));
+}
+
 // Dense [A | I] (n x 2n, row-major) of the base operator for Gauss-Jordan inversion.
 __global__ void k_dense_aug(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const double* __restrict__ K, const double* __restrict__ M, double inv_dt,
@@ -530,8 +542,29 @@ static MgDepth* build_depth(mg_ctx* c, int mesh, double dt) {
                                         d->dinv64.as<double>(), d->dinv32.as<float>(), c->flag.as<int>());
     k_ell_scaled<<<nblk(nW), 256, 0, s>>>(nW, m.n, m.ell_col.as<int32_t>(), d->L64.as<double>(),
                                          d->dinv64.as<double>(), d->LD32.as<float>());
+    DBuf bound;
+    bound.ensure(sizeof(unsigned));
+    MG_CUDA(cudaMemsetAsync(bound.p, 0, sizeof(unsigned), s));
+    k_ell_gershgorin<<<nblk(m.n), 256, 0, s>>>(m.n, m.ell_W, d->L64.as<double>(), d->dinv64.as<double>(),
+                                               bound.as<unsigned>());
     MG_CUDA(cudaGetLastError());
+    unsigned bits = 0;
+    MG_CUDA(cudaMemcpyAsync(&bits, bound.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(&d->lam, &bits, sizeof(float));
     return d;
+}
+
+void smoother_weights(const MgDepth& d, const mg_solver_opts& so, bool per_column, int nu, float* w) {
+    const double omega = so.omega > 0.0 ? so.omega : 0.7;
+    const bool cheb = !per_column && so.smoother == MG_SMOOTH_CHEBYSHEV && d.lam > 0.0f;
+    const double b = d.lam, a = b / (so.cheb_ratio > 0.0 ? so.cheb_ratio : 30.0);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < nu; ++k) {
+        // k-th root of the first-kind Chebyshev polynomial of degree nu mapped to [a, b]
+        const double theta = 0.5 * (b + a) + 0.5 * (b - a) * std::cos(pi * (2 * k + 1) / (2.0 * nu));
+        w[k] = cheb ? (float)(1.0 / theta) : (float)omega;
+    }
 }
 
 // Dense FP32 inverse of M/dt + K on a small base mesh (Gauss-Jordan on [A | I]

@@ -52,6 +52,8 @@ class mg_solver_opts(C.Structure):
         ("rows_per_block", C.c_int),
         ("coarse_rows_per_block", C.c_int),
         ("base_tiles", C.c_int),
+        ("smoother", C.c_int),
+        ("cheb_ratio", C.c_double),
     ]
 
 

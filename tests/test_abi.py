@@ -47,9 +47,12 @@ def test_defaults_are_sane(libpath):
     so = lib.mg_solver_opts()
     L.mg_solver_defaults(ctypes.byref(so))
     assert so.cg_tol == 1e-13 and so.max_cg > 0 and so.precision == lib.MG_FP64
+    # the last fields: a binding whose layout drifted from the header reads garbage here
+    assert so.smoother == 0 and so.cheb_ratio == 30.0 and so.smooth == 5 and so.base_tiles == 0
     o = lib.mg_opts()
     L.mg_opts_defaults(ctypes.byref(o))
     assert o.levels == 2 and o.m[0] == 16 and o.relax == 1 and o.restrict_mode == 2
+    assert o.solver.cheb_ratio == 30.0 and o.solver.newton_tol == 1e-8
 
 
 def test_null_context_is_rejected(libpath):
