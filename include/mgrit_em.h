@@ -135,8 +135,9 @@ typedef enum { MG_PRECOND_JACOBI = 0, MG_PRECOND_MULTIGRID = 1 } mg_precond;
  * roots of the first-kind Chebyshev polynomial on [lam / cheb_ratio, lam], lam
  * the Gershgorin bound max_i sum_j |L_ij| / L_ii of the depth's operator, so that
  * the sweeps together damp that whole upper part of the spectrum of D^-1 L (the
- * factors commute, so the V-cycle stays symmetric).  Steps of nonlinear meshes
- * (per-column Jacobians) always use damped Jacobi. */
+ * factors commute, so the V-cycle stays symmetric).  Newton corrections of
+ * nonlinear meshes take as lam the largest such bound over the Jacobians of all
+ * columns, recomputed on the device with every Jacobian. */
 typedef enum { MG_SMOOTH_CHEBYSHEV = 0, MG_SMOOTH_JACOBI = 1 } mg_smoother;
 
 /* How a batched step runs: MG_PATH_CLUSTER = one persistent launch, a thread-block
@@ -163,7 +164,7 @@ typedef struct {
     int precond;        /* mg_precond                                                      */
     int smooth;         /* smoothing sweeps before and after each coarse correction (1..8),
                            0 = library choice (5)                                          */
-    double omega;       /* MG_SMOOTH_JACOBI weight (and of Newton steps' smoothing)        */
+    double omega;       /* MG_SMOOTH_JACOBI weight                                         */
     int path;           /* mg_path                                                         */
     /* nonlinear steps (meshes with a Brauer-law material, Sec. 5): damped Newton,
      * each correction J delta = -F solved by the PCG above (FP64 form, multigrid
@@ -186,8 +187,8 @@ typedef struct {
 
 /* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,
  * inner_tol 1e-5, max_cg 2000, max_refine 30, FP64, multigrid with 5 Chebyshev
- * sweeps on [lam/30, lam] before and after each coarse correction (Newton steps:
- * 5 damped-Jacobi sweeps of weight 0.7); newton_tol 1e-8, max_newton 100,
+ * sweeps on [lam/30, lam] before and after each coarse correction (omega 0.7 for
+ * MG_SMOOTH_JACOBI); newton_tol 1e-8, max_newton 100,
  * max_halvings 40, newton_lin_tol 1e-6). */
 void mg_solver_defaults(mg_solver_opts* opts);
 

@@ -475,10 +475,17 @@ constexpr int RPPF = NTB / TPRF;   // rows per pass
     const int _i1 = min((D).n, (rb + 1) * (D).rbs);           \
     for (int i = rb * (D).rbs + threadIdx.x / TPRF; i < _i1; i += RPPF)
 
+// sweep weight: w, divided by the device-side spectral bound *lam when given
+__device__ __forceinline__ float sweep_weight(float w, const unsigned* lam) {
+    return lam ? w / __uint_as_float(__ldg(lam)) : w;
+}
+
 // x = w D^-1 r, s = r - w (L D^-1) r
 template <class RT, bool PC>
-__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth_first(Depth D, const RT* rin_base, float w) {
+__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth_first(Depth D, const RT* rin_base, float w0,
+                                                                  const unsigned* lam) {
     phase_begin();
+    const float w = sweep_weight(w0, lam);
     ROWS_F(D, t, rb, i) {
         const RT* rin = tv(rin_base, D.n, t);
         RT rv[VF];
@@ -502,8 +509,9 @@ __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth_first(Depth D, const
 // partial (r, x) if rtop is given (last sweep on the finest level)
 template <class RT, bool PC>
 __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth(Depth D, const float* src_base, float* dst_base, const RT* rtop_base,
-                                                 float w, double* part) {
+                                                 float w0, const unsigned* lam, double* part) {
     phase_begin();
+    const float w = sweep_weight(w0, lam);
     double rz[VF] = {0.0, 0.0, 0.0, 0.0};
     {
         ROWS_F(D, t, rb, i) {
@@ -996,6 +1004,7 @@ struct GraphPlan {
     int smoother = 0;
     double cheb_ratio = 0.0;
     float wsm[MG_MAX_DEPTH][MG_MAX_NU] = {};  // sweep weights of each depth's pre-smoothing
+    bool wlam = false;  // per-column operators with Chebyshev weights: divide by pco.lam[d]
     std::vector<DBuf> bufs;
     DBuf args, cols, part;
     std::vector<Depth> depth;
@@ -1044,12 +1053,13 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
     for (int d = 0; d < nd - 1; ++d) {
         Depth& D = P.depth[d];
         const float* ws = P.wsm[d];
-        if (d == 0) pdl_launch(kb_smooth_first<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, ws[0]);
-        else pdl_launch(kb_smooth_first<float, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.r, ws[0]);
+        const unsigned* lam = P.wlam ? P.pco.lam + d : nullptr;
+        if (d == 0) pdl_launch(kb_smooth_first<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, ws[0], lam);
+        else pdl_launch(kb_smooth_first<float, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.r, ws[0], lam);
         int sl = 0;
         for (int sw = 1; sw < P.nu; ++sw) {
             pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr,
-                       ws[sw], nullptr);
+                       ws[sw], lam, nullptr);
             sl ^= 1;
         }
         sel[d] = sl;
@@ -1079,7 +1089,8 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
     if (nd == 1) {
         // z is final; a zero-weight sweep accumulates (r, z) for a single-level hierarchy
         Depth& D = P.depth[0];
-        pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.x, nullptr, rtop, 0.0f, part);
+        pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.x, nullptr, rtop, 0.0f,
+                   (const unsigned*)nullptr, part);
         return;
     }
     for (int d = nd - 2; d >= 0; --d) {
@@ -1094,7 +1105,7 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
             const bool top = last && d == 0;
             pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa,
                        last ? nullptr : (sl ? D.sa : D.sb), top ? rtop : nullptr, P.wsm[d][P.nu - 1 - sw],
-                       top ? part : nullptr);
+                       P.wlam ? P.pco.lam + d : nullptr, top ? part : nullptr);
             sl ^= 1;
         }
     }
@@ -1172,8 +1183,11 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         P->omega = so.omega > 0.0 ? (float)so.omega : 0.7f;
         P->smoother = so.smoother;
         P->cheb_ratio = so.cheb_ratio;
+        // per-column Jacobians: weights for a unit bound, divided on the device by the
+        // bound of the current Jacobians (damped Jacobi without one)
+        P->wlam = P->pc && P->pco.lam && so.smoother == MG_SMOOTH_CHEBYSHEV;
         for (int d = 0; d < (int)op.mg.size() && d < MG_MAX_DEPTH; ++d)
-            smoother_weights(*op.mg[d], so, P->pc, P->nu, P->wsm[d]);
+            smoother_weights(P->pc ? (P->wlam ? 1.0 : 0.0) : op.mg[d]->lam, so, P->nu, P->wsm[d]);
         const MeshLevel& m0 = c->meshes[op.mesh];
         const int nd = so.precond == MG_PRECOND_MULTIGRID ? (int)op.mg.size() : 1;
         for (int d = 0; d < nd; ++d) {

@@ -182,9 +182,10 @@ const int8_t* ctx_pwm_table(mg_ctx* c, int64_t N, double T);
 const double* ctx_wave_table(mg_ctx* c, int64_t N, double T, int kind);
 // Lookups that never allocate: null if the operator / PWM table was not built yet.
 const StepOp* ctx_find_step_op(const mg_ctx* c, int mesh, double dt);
-// Weights of the nu smoothing sweeps of one pre-smoothing on depth d (post-smoothing
-// takes them in reverse order): Chebyshev roots on [lam / ratio, lam] or omega.
-void smoother_weights(const MgDepth& d, const mg_solver_opts& so, bool per_column, int nu, float* w);
+// Weights of the nu smoothing sweeps of one pre-smoothing (post-smoothing takes them
+// in reverse order): reciprocal Chebyshev roots on [lam / ratio, lam] when the
+// options ask for Chebyshev smoothing and lam > 0, else omega.
+void smoother_weights(double lam, const mg_solver_opts& so, int nu, float* w);
 inline int smooth_sweeps(const mg_solver_opts& so) { return so.smooth > 0 ? so.smooth : 5; }
 const int8_t* ctx_find_pwm_table(const mg_ctx* c, int64_t N, double T);
 const double* ctx_find_wave_table(const mg_ctx* c, int64_t N, double T, int kind);
@@ -240,6 +241,9 @@ struct PcOperator {
     int band_u = 0, band_stride = 0;
     const double* R = nullptr;      // residual: the system solved is J delta = -R
     const int* state = nullptr;     // only columns with state 1 are solved
+    // per depth, device: Gershgorin bound of D^-1 J over all columns (float bits),
+    // refreshed with every Jacobian; the plan's Chebyshev weights are divided by it
+    const unsigned* lam = nullptr;
 };
 GraphPlan* graph_plan_pc(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so, const PcOperator& pco);
 double* graph_plan_solution(GraphPlan* p);

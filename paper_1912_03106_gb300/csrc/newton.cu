@@ -295,22 +295,38 @@ __global__ void __launch_bounds__(NTB) kn_galerkin(int64_t nWc, int64_t nWf, con
     Jc32[o] = (float)v;
 }
 
-// 1/diag per row and column
+// 1/diag per row and column, and into *lam the maximum over rows and columns of the
+// Gershgorin ratio sum_j |J_ij| / J_ii (rounded up to float; positive floats order
+// like their bits, so the maximum is an unsigned atomicMax, one per block)
 __global__ void __launch_bounds__(NTB) kn_dinv(int n, int W, int nrb, const int32_t* __restrict__ col,
-                                               const double* J64, float* dinv32, int* flag) {
+                                               const double* J64, float* dinv32, int* flag, unsigned* lam) {
     const int t = blockIdx.x / nrb, rb = blockIdx.x % nrb;
     const int lc = threadIdx.x % G;
     const int i1 = min(n, (rb + 1) * RBS);
     const double* jt = J64 + (size_t)t * W * n * G + lc;
+    unsigned gmax = 0u;
     for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
-        double d = 0.0;
-        for (int w = 0; w < W; ++w)
-            if (__ldg(col + w * n + i) == i) d += jt[((size_t)w * n + i) * G];
+        double d = 0.0, a = 0.0;
+        for (int w = 0; w < W; ++w) {
+            const double v = jt[((size_t)w * n + i) * G];
+            a += fabs(v);
+            if (__ldg(col + w * n + i) == i) d += v;
+        }
         if (!(d > 0.0)) {
             atomicExch(flag, 1);
             d = 1.0;
         }
         dinv32[((size_t)t * n + i) * G + lc] = (float)(1.0 / d);
+        gmax = max(gmax, __float_as_uint(__double2float_ru(a / d)));
+    }
+    __shared__ unsigned wmax[NTB / 32];
+    gmax = __reduce_max_sync(0xffffffffu, gmax);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = gmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned m = 0u;
+        for (int q = 0; q < NTB / 32; ++q) m = max(m, wmax[q]);
+        atomicMax(lam, m);
     }
 }
 
@@ -686,6 +702,8 @@ struct NewtonPlan {
     Cols cols{};
     int* flags_h = nullptr;  // pinned
     GraphPlan* pcg = nullptr;
+    mg_solver_opts pso{};  // options the PCG graph was built with
+    unsigned* lam = nullptr;  // per depth: Gershgorin bound of the current Jacobians
     std::vector<int> mesh_of_depth;
     ~NewtonPlan() {
         if (pcg) graph_plan_delete(pcg);
@@ -702,9 +720,24 @@ static void* nalloc(NewtonPlan& P, cudaStream_t s, size_t bytes) {
     return P.bufs.back().p;
 }
 
+// the options the correction's PCG graph depends on
+static bool same_pcg_shape(const mg_solver_opts& a, const mg_solver_opts& b) {
+    return smooth_sweeps(a) == smooth_sweeps(b) && a.omega == b.omega && a.smoother == b.smoother &&
+           a.cheb_ratio == b.cheb_ratio && a.rows_per_block == b.rows_per_block &&
+           a.coarse_rows_per_block == b.coarse_rows_per_block && a.base_tiles == b.base_tiles;
+}
+
 static NewtonPlan* newton_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so) {
     for (auto* p : c->nplans)
-        if (p->op == &op && p->ntile == ntile) return p;
+        if (p->op == &op && p->ntile == ntile) {
+            if (!same_pcg_shape(p->pso, so)) {  // rebuild the correction's graph for new options
+                graph_plan_delete(p->pcg);
+                p->pcg = nullptr;
+                p->pcg = graph_plan_pc(c, op, ntile, so, p->pco);
+                p->pso = so;
+            }
+            return p;
+        }
     auto* P = new NewtonPlan();
     cudaStream_t s = c->stream;
     try {
@@ -754,9 +787,12 @@ static NewtonPlan* newton_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_
         P->cols.first = P->cols.its + kpad;
         P->cols.flags = P->cols.first + kpad;
         P->pco.state = P->cols.state;
+        P->lam = (unsigned*)nalloc(*P, s, MG_MAX_DEPTH * sizeof(unsigned));
+        P->pco.lam = P->lam;
         MG_CUDA(cudaMallocHost(&P->flags_h, 4 * sizeof(int)));
         MG_CUDA(cudaStreamSynchronize(s));
         P->pcg = graph_plan_pc(c, op, ntile, so, P->pco);
+        P->pso = so;
         c->nplans.push_back(P);
         return P;
     } catch (...) {
@@ -846,6 +882,7 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
                                                                N0.jc_e.as<int32_t>(), N0.jc_w.as<double>(), P->yN,
                                                                P->J64[0], P->pco.d[0].J32);
         launches += 2;
+        MG_CUDA(cudaMemsetAsync(P->lam, 0, MG_MAX_DEPTH * sizeof(unsigned), s));
         for (int d = 0; d < nd; ++d) {
             const MeshLevel& md = c->meshes[P->mesh_of_depth[d]];
             const int64_t nW = (int64_t)md.ell_W * md.n;
@@ -859,7 +896,7 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
             }
             const int nrb = (int)((md.n + RBS - 1) / RBS);
             kn_dinv<<<ntile * nrb, NTB, 0, s>>>((int)md.n, md.ell_W, nrb, md.ell_col.as<int32_t>(), P->J64[d],
-                                                P->pco.d[d].dinv32, c->flag.as<int>());
+                                                P->pco.d[d].dinv32, c->flag.as<int>(), P->lam + d);
             kn_ld<<<dim3(nblk(nW, NTB / G), ntile), NTB, 0, s>>>(nW, (int)md.n, md.ell_col.as<int32_t>(),
                                                                  P->pco.d[d].J32, P->pco.d[d].dinv32,
                                                                  P->pco.d[d].LD32);

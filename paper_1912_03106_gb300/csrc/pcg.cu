@@ -979,7 +979,7 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
     a.nu = smooth_sweeps(so);
     a.omega = so.omega > 0.0 ? (float)so.omega : 0.7f;
     a.nd = a.precond == 1 ? (int)op.mg.size() : 1;
-    for (int d = 0; d < a.nd; ++d) smoother_weights(*op.mg[d], so, false, a.nu, a.wsm[d]);
+    for (int d = 0; d < a.nd; ++d) smoother_weights(op.mg[d]->lam, so, a.nu, a.wsm[d]);
     a.base_inv = (a.precond == 1 && op.base_inv.p) ? op.base_inv.as<float>() : nullptr;
     // work vectors: each is ntile * n_d * KT elements
     int wsi = 0;
@@ -1153,7 +1153,7 @@ void static_step(void* arg) {
     a.nu = smooth_sweeps(so);
     a.omega = so.omega > 0.0 ? (float)so.omega : 0.7f;
     a.nd = a.precond == 1 ? (int)op->mg.size() : 1;
-    for (int d = 0; d < a.nd; ++d) smoother_weights(*op->mg[d], so, false, a.nu, a.wsm[d]);
+    for (int d = 0; d < a.nd; ++d) smoother_weights(op->mg[d]->lam, so, a.nu, a.wsm[d]);
     a.base_inv = (a.precond == 1 && op->base_inv.p) ? op->base_inv.as<float>() : nullptr;
     // carve the work vectors out of the static array (256-byte aligned pieces)
     const size_t e0 = (size_t)ntile * m0.n * KT;

@@ -555,10 +555,10 @@ static MgDepth* build_depth(mg_ctx* c, int mesh, double dt) {
     return d;
 }
 
-void smoother_weights(const MgDepth& d, const mg_solver_opts& so, bool per_column, int nu, float* w) {
+void smoother_weights(double lam, const mg_solver_opts& so, int nu, float* w) {
     const double omega = so.omega > 0.0 ? so.omega : 0.7;
-    const bool cheb = !per_column && so.smoother == MG_SMOOTH_CHEBYSHEV && d.lam > 0.0f;
-    const double b = d.lam, a = b / (so.cheb_ratio > 0.0 ? so.cheb_ratio : 30.0);
+    const bool cheb = so.smoother == MG_SMOOTH_CHEBYSHEV && lam > 0.0;
+    const double b = lam, a = b / (so.cheb_ratio > 0.0 ? so.cheb_ratio : 30.0);
     const double pi = 3.14159265358979323846;
     for (int k = 0; k < nu; ++k) {
         // k-th root of the first-kind Chebyshev polynomial of degree nu mapped to [a, b]

@@ -86,6 +86,30 @@ def test_newton_step_matches_oracle(meshes, nl, level, k):
     assert abs(st["newton_iters"] - sum(its)) <= k, (st["newton_iters"], sum(its))
 
 
+def test_newton_smoothers_give_the_same_step(meshes, nl):
+    """Chebyshev smoothing of the per-column Jacobians (interval from the device-side
+    Gershgorin bound of every Jacobian) and damped Jacobi solve the same Newton
+    corrections: both steps are the oracle's to 1e-10, and Chebyshev needs fewer
+    PCG iterations.  Switching the smoother on one context also rebuilds the
+    correction's cached graph."""
+    model, ctx, ids = nl
+    k = 20
+    u, its = oracle_run(meshes, model, 1, k)
+    n = u.shape[1]
+    want = u[1:k + 1].T
+    cg = {}
+    for smoother in (1, 0, 1):
+        out = torch.zeros((n, k), dtype=torch.float64, device="cuda")
+        _, st = ctx.mg_step(ids[1], N, T, dev(u[:k].T), out, i0=1, istride=1,
+                            solver=api.solver_opts(smoother=smoother))
+        err = np.linalg.norm(out.cpu().numpy() - want, axis=0) / np.linalg.norm(want, axis=0)
+        assert err.max() <= 1e-10, (smoother, err.max())
+        assert st["worst_status"] == "MG_OK"
+        cg.setdefault(smoother, []).append(st["cg_iters"])
+    assert cg[1][0] == cg[1][1], cg  # the rebuilt Jacobi graph repeats the first run
+    assert cg[0][0] < cg[1][0], cg
+
+
 def test_newton_step_from_a_converged_guess(meshes, nl):
     """Started at the solution, every column stops after one (negligible) correction."""
     model, ctx, ids = nl
