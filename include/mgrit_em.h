@@ -192,6 +192,17 @@ typedef struct {
  * max_halvings 40, newton_lin_tol 1e-6). */
 void mg_solver_defaults(mg_solver_opts* opts);
 
+/* The smoothing weights the V-cycle uses on a depth whose Gershgorin bound of
+ * D^-1 L is lam (host computation, no device work, no context): w[0 .. nu-1] of
+ * one pre-smoothing, post-smoothing takes them in reverse order.  With
+ * MG_SMOOTH_CHEBYSHEV and lam > 0 they are the reciprocals of the roots of the
+ * first-kind Chebyshev polynomial of degree nu on [lam / cheb_ratio, lam] (cheb_ratio
+ * 0: 30), so that prod_s (1 - w_s x) has the smallest maximum modulus on that
+ * interval among degree-nu polynomials equal to 1 at x = 0; otherwise every weight is
+ * omega (0: 0.7).  w: nu floats, caller-owned.  MG_EINVAL for bad options, nu outside
+ * 1..8 or lam < 0. */
+mg_status mg_smoother_weights(const mg_solver_opts* opts, double lam, int nu, float* w);
+
 typedef struct {
     int iters;                /* MGRIT iterations (coarse-grid corrections)        */
     int n_hist;               /* entries of res_hist                               */

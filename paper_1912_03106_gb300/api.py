@@ -294,6 +294,18 @@ def mg_batch_solve(ctxs, N, T, a0, out, opts, max_threads=0):
     return rc, [L.STATUS.get(v, v) for v in st], [stats_dict(s) for s in stats]
 
 
+def mg_smoother_weights(lam, nu, solver=None):
+    """Weights of one pre-smoothing of nu sweeps on a depth with Gershgorin bound
+    lam (host only): Chebyshev roots on [lam / cheb_ratio, lam] or omega."""
+    lib = L.load()
+    so = solver or solver_opts()
+    w = (C.c_float * max(1, nu))()
+    rc = lib.mg_smoother_weights(C.byref(so), lam, nu, w)
+    if rc != L.MG_OK:
+        raise L.MgError(rc, "mg_smoother_weights: bad input")
+    return [w[i] for i in range(nu)]
+
+
 def mg_choose_levels(k_list, ms_list, N, max_levels=5):
     """Sec. 4.1's coarsening heuristic on measured step times (host only).
     Returns (levels, [m_0, ..., m_{levels-2}])."""

@@ -758,6 +758,16 @@ void mg_solver_defaults(mg_solver_opts* s) {
     s->cheb_ratio = 30.0;
 }
 
+mg_status mg_smoother_weights(const mg_solver_opts* so, double lam, int nu, float* w) {
+    if (!so || !w || nu < 1 || nu > MG_MAX_NU || !(lam >= 0.0) ||
+        (so->smoother != MG_SMOOTH_CHEBYSHEV && so->smoother != MG_SMOOTH_JACOBI) ||
+        !(so->cheb_ratio == 0.0 || (so->cheb_ratio > 1.0 && so->cheb_ratio <= 1e4)) ||
+        !(so->omega >= 0.0 && so->omega < 2.0))
+        return MG_EINVAL;
+    smoother_weights(lam, *so, nu, w);
+    return MG_OK;
+}
+
 void mg_opts_defaults(mg_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));

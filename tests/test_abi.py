@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -53,6 +54,48 @@ def test_defaults_are_sane(libpath):
     L.mg_opts_defaults(ctypes.byref(o))
     assert o.levels == 2 and o.m[0] == 16 and o.relax == 1 and o.restrict_mode == 2
     assert o.solver.cheb_ratio == 30.0 and o.solver.newton_tol == 1e-8
+
+
+@pytest.mark.parametrize("ratio", [10.0, 30.0, 100.0])
+@pytest.mark.parametrize("nu", [1, 2, 3, 5, 8])
+def test_chebyshev_smoother_weights_are_minimax(libpath, nu, ratio):
+    """The smoothing polynomial p(x) = prod_s (1 - w_s x) of the library's weights
+    is the scaled Chebyshev polynomial of [a, b] = [lam/ratio, lam]: it
+    equioscillates with modulus 1/T_nu((b+a)/(b-a)) at the nu+1 Chebyshev extrema
+    of [a, b] (which only the right roots achieve), never exceeds that modulus on
+    [a, b], and stays within (0, 1] on [0, a)."""
+    from paper_1912_03106_gb300 import api
+
+    lam = 2.46
+    w = np.array(api.mg_smoother_weights(lam, nu, api.solver_opts(cheb_ratio=ratio)), dtype=np.float64)
+    b, a = lam, lam / ratio
+    z0 = (b + a) / (b - a)
+    bound = 1.0 / np.cosh(nu * np.arccosh(z0))
+
+    def p(x):
+        return np.prod(1.0 - np.outer(x, w), axis=1)
+
+    k = np.arange(nu + 1)
+    xk = (b + a) / 2 + (b - a) / 2 * np.cos(k * np.pi / nu)
+    pk = p(xk)
+    assert np.allclose(np.abs(pk), bound, rtol=1e-4, atol=0), (pk, bound)
+    assert np.all(np.sign(pk[:-1]) != np.sign(pk[1:]))  # alternating signs
+    x = np.linspace(a, b, 20001)
+    assert np.abs(p(x)).max() <= bound * (1 + 1e-4)
+    x0 = np.linspace(0.0, a, 2001, endpoint=False)
+    assert np.all(p(x0) > 0.0) and np.all(p(x0) <= 1.0 + 1e-6) and p(np.zeros(1))[0] == 1.0
+
+
+def test_jacobi_smoother_weights_and_bad_input(libpath):
+    from paper_1912_03106_gb300 import api, lib
+
+    assert api.mg_smoother_weights(2.46, 4, api.solver_opts(smoother=1, omega=0.6)) == pytest.approx([0.6] * 4)
+    # without a bound (lam = 0) Chebyshev falls back to omega
+    assert api.mg_smoother_weights(0.0, 3, api.solver_opts(omega=0.7)) == pytest.approx([0.7] * 3)
+    for lam, nu, kw in ((2.0, 0, {}), (2.0, 9, {}), (-1.0, 2, {}), (2.0, 2, dict(smoother=2)),
+                        (2.0, 2, dict(cheb_ratio=1.0))):
+        with pytest.raises(lib.MgError):
+            api.mg_smoother_weights(lam, nu, api.solver_opts(**kw))
 
 
 def test_null_context_is_rejected(libpath):
