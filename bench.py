@@ -208,6 +208,25 @@ def instances_run(args):
         s[0].close()
 
 
+def workload_config(n_fine, n_coarse, world):
+    """The workload keys both arms report (the MGRIT arm adds its solver settings)."""
+    return {"workload": WORKLOAD, "dofs": n_fine, "N": N_STEPS, "T_s": T_END, "levels": 3, "m": [16, 16],
+            "relax": "FCF", "space_levels": [n_fine, n_coarse, n_coarse], "error_target": ERR_TARGET,
+            "l2_flush": "inputs larger than L2 (600 MB trajectory per solve)", "parallelism": f"replicas x{world}"}
+
+
+def max_over_ranks(t, world, device):
+    """The slowest rank's time: the whole job ends with it (t itself on one rank)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as td
+
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    td.all_reduce(tt, op=td.ReduceOp.MAX)
+    return float(tt)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -392,12 +411,7 @@ def run_ours(args, rank, world, local):
     dev_s = e0.elapsed_time(e1) / 1e3
     t_step = dev_s / args.steps
     mgrit_out = out.clone()  # the last timed solve
-    if world > 1:
-        import torch.distributed as td
-
-        tt = torch.tensor([t_step], dtype=torch.float64, device=dev)
-        td.all_reduce(tt, op=td.ReduceOp.MAX)
-        t_step = float(tt)
+    t_step = max_over_ranks(t_step, world, dev)
     value = world * N / t_step
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -410,7 +424,7 @@ def run_ours(args, rank, world, local):
     for _ in range(args.steps):
         ctx.mg_solve_host(N, T, a0_np, out_np, opts)
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
 
     roof = roofline(ctx, ids, N, T, stream)
 
@@ -454,13 +468,9 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dofs": n, "N": N, "T_s": T, "levels": 3, "m": [16, 16], "relax": "FCF",
-                   "space_levels": [n, ctx.mg_num_dofs(ids[0]), ctx.mg_num_dofs(ids[0])],
-                   "mgrit_tol_rel": tol, "error_target": ERR_TARGET,
-                   "precond": "multigrid V(%d,%d), Chebyshev smoothing on [lam/%g, lam], FP32, dense base inverse"
-                              % (dso.smooth, dso.smooth, dso.cheb_ratio),
-                   "l2_flush": "inputs larger than L2 (600 MB trajectory per solve)",
-                   "parallelism": f"replicas x{world}"},
+        "config": dict(workload_config(n, ctx.mg_num_dofs(ids[0]), world), mgrit_tol_rel=tol,
+                       precond="multigrid V(%d,%d), Chebyshev smoothing on [lam/%g, lam], FP32, dense base inverse"
+                               % (dso.smooth, dso.smooth, dso.cheb_ratio)),
         "mgrit": {"wall_s": t_step, "iters": st["iters"], "res_hist": st["res_hist"],
                   "step_tol_ratio": STEP_TOL_RATIO, "tolerance_calibration": calib,
                   "max_rel_err_vs_reference": max_err, "step_solves": st["step_solves"],
@@ -592,7 +602,7 @@ def run_reference(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD},
+        "config": workload_config(P.n, len(ms[0].interior_nodes()), world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{sample} sequential backward-Euler steps of the 18,240-DOF model per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
