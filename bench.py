@@ -474,7 +474,8 @@ def run_ours(args, rank, world, local):
         "mgrit": {"wall_s": t_step, "iters": st["iters"], "res_hist": st["res_hist"],
                   "step_tol_ratio": STEP_TOL_RATIO, "tolerance_calibration": calib,
                   "max_rel_err_vs_reference": max_err, "step_solves": st["step_solves"],
-                  "batched_steps": st["batched_steps"], "pcg_iters": st["cg_iters"]},
+                  "batched_steps": st["batched_steps"], "pcg_iters": st["cg_iters"],
+                  "step_solves_per_s": st["step_solves"] / t_step},
         "gpu_sequential": {"wall_s": seq_s, "time_steps_per_s": N / seq_s, "pcg_iters": seq_st["cg_iters"],
                            "step_cg_tol": seq_tol, "smoothing": SEQ_SMOOTHING, "tolerance_calibration": seq_calib,
                            "max_rel_err_vs_reference": seq_err},
