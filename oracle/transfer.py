@@ -6,7 +6,7 @@ coarse edge takes the mean of the edge's two end values.  Across several
 refinements P_s is the product of the single-level operators.  All operators act
 on interior DOFs; Dirichlet values are zero.
 
-Restrictions R_s (Algorithm 1, line 5):
+Restrictions R_s (Algorithm 1, restriction step):
   state u:   nodal interpolation onto the coarse mesh = injection at coarse nodes
   residual:  mode 0  injection (nodal interpolation, as for the state)
              mode 1  P_s^T

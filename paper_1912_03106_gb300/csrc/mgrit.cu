@@ -78,7 +78,7 @@ __global__ void k_sum_partials(int nb, const double* __restrict__ partial, doubl
     if (threadIdx.x == 0) out[0] = red[0];
 }
 
-// Restriction (Algorithm 1, lines 4-5): W[:, c] = R_s u(cm) (injection at coarse
+// Restriction (Algorithm 1, restriction step): W[:, c] = R_s u(cm) (injection at coarse
 // nodes), g2[:, c] = R_s r_c with mode 0 injection, 1 P^T, 2 diag(P^T 1)^-1 P^T.
 __global__ void k_restrict(int64_t nc, int64_t NT, const double* __restrict__ U0, int64_t ld,
                            const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ inj,
@@ -102,7 +102,7 @@ __global__ void k_restrict(int64_t nc, int64_t NT, const double* __restrict__ U0
     }
 }
 
-// FAS right-hand side of the coarse level (Algorithm 1, line 6):
+// FAS right-hand side of the coarse level (Algorithm 1, coarse problem):
 // G_0 = u2_0 + g2_0, G_c = u2_c - Phi_c(u2_{c-1}) + g2_c; coarse iterate v = u2.
 __global__ void k_fas_rhs(int64_t nc, int64_t Nc, const double* __restrict__ W, const double* __restrict__ g2,
                           const double* __restrict__ Vc, int64_t ldw, LevelView Gv, LevelView Uv) {
@@ -117,7 +117,7 @@ __global__ void k_fas_rhs(int64_t nc, int64_t Nc, const double* __restrict__ W, 
     }
 }
 
-// Correction (Algorithm 1, lines 7-9): u(cm) += P_s (v_c - u2_c), c = 1..NT.
+// Correction (Algorithm 1, coarse-grid correction): u(cm) += P_s (v_c - u2_c), c = 1..NT.
 __global__ void k_correct(int64_t nf, int64_t NT, double* __restrict__ U0, int64_t ld, LevelView Vv,
                           const double* __restrict__ W, int64_t ldw, const int32_t* __restrict__ p_ptr,
                           const int32_t* __restrict__ p_col, const double* __restrict__ p_val) {
