@@ -98,6 +98,27 @@ def test_jacobi_smoother_weights_and_bad_input(libpath):
             api.mg_smoother_weights(lam, nu, api.solver_opts(**kw))
 
 
+def test_header_is_plain_c(tmp_path):
+    """include/mgrit_em.h is a C header: a C99 translation unit that includes it and
+    calls into it compiles without warnings (no C++ types cross the boundary)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "mgrit_em.h"\n'
+                   "int main(void) {\n"
+                   "    mg_solver_opts so; mg_opts o; float w[5];\n"
+                   "    mg_solver_defaults(&so); mg_opts_defaults(&o);\n"
+                   "    return (int)mg_smoother_weights(&so, 2.0, 5, w) + o.levels;\n"
+                   "}\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_null_context_is_rejected(libpath):
     from paper_1912_03106_gb300 import lib
 
