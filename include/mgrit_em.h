@@ -52,7 +52,9 @@ typedef enum {
     MG_ENEWTON = -6,       /* Newton did not converge (Sec. 5: poor initial guess) */
     MG_EMGRIT_MAXIT = -7,  /* MGRIT reached max_iter before the tolerance       */
     MG_ETIMEOUT = -8,      /* a bounded device wait ran out                     */
-    MG_ESTATE = -9         /* call order violated (e.g. solve before set-up)    */
+    MG_ESTATE = -9,        /* call order violated (e.g. solve before set-up)    */
+    MG_ESTALLED = -10,     /* MGRIT residual stopped decreasing above the tolerance */
+    MG_ENONFINITE = -11    /* a step solve met a NaN or infinity (e.g. in an input state) */
 } mg_status;
 
 /* ------------------------------------------------------------------ context */
@@ -227,7 +229,14 @@ typedef struct {
  * from x_in[:, c] (or from the guess); a column whose Newton iteration fails
  * reports MG_ENEWTON and keeps its last iterate.
  * Node-major layouts with leading dimensions ld_in, ld_out >= k.
- * stats may be NULL (then the call does not synchronise). */
+ * Each column's linear solve stops at ||b - L x|| <= cg_tol ||b|| (refine_tol for
+ * FP32+refinement) or at the rounding floor of its FP64 residual, whichever is
+ * larger: ||b - L x|| <= gamma_{W+1} || |b| + |L| |x| ||, gamma_k = k u / (1 - k u),
+ * u = 2^-53, W the stored entries per row; an initial guess within 4 gamma_{W+1}
+ * of that norm is returned unchanged, so re-solving a step from its own solution
+ * gives that solution back.
+ * stats may be NULL; then the call does not synchronise and per-column solver
+ * failures (MG_ECG_MAXIT, MG_ENEWTON) are not reported: pass stats to get them. */
 mg_status mg_step(mg_ctx* ctx, int level, int64_t N, double T, int64_t dt_mult, int k,
                   int64_t i0, int64_t istride, const double* x_in, int64_t ld_in,
                   double* x_out, int64_t ld_out, int guess, const mg_solver_opts* opts,
@@ -317,7 +326,11 @@ void mg_opts_defaults(mg_opts* opts);
  * N must be divisible by m[0] * ... * m[L-2].  a0: n doubles; out: (N+1)*n
  * doubles, time-major (device pointers).  Iterate: relax (F or FCF), C-point
  * residual norm, stop test, coarse-grid correction.  Returns MG_EMGRIT_MAXIT if
- * the tolerance was not reached (out holds the last iterate). */
+ * the tolerance was not reached in max_iter iterations and MG_ESTALLED if, with the
+ * residual rule, five iterations in a row brought no residual below 0.9 times the
+ * smallest one so far (the iterate is then at the accuracy its step solves allow);
+ * out holds the last iterate and mg_last_error() the last residual.  Per-column
+ * step failures are returned (MG_ECG_MAXIT, MG_ENEWTON) with or without stats. */
 mg_status mg_solve(mg_ctx* ctx, int64_t N, double T, const double* a0, double* out,
                    const mg_opts* opts, mg_stats* stats);
 

@@ -80,6 +80,11 @@ struct CallArgs {
     int k;
     double tol2;        // FP64 form: cg_tol^2; FP32+refine: refine_tol^2
     double inner_tol2;  // FP32+refine inner reduction^2
+    // rounding floor of the FP64 residual b - L x: a column whose computed residual
+    // satisfies ||r||^2 <= fl_acc2 * S^2, S = || |b| + |L| |x| ||, is a solution to
+    // working precision (its initial guess is kept, refinement stops); the PCG
+    // iteration stops at fl_stop2 * S^2 (0: no floor)
+    double fl_stop2, fl_acc2;
     int max_it;
     int max_refine;
 };
@@ -101,8 +106,9 @@ struct Depth {
 };
 
 struct Cols {
-    double *bb, *gam, *beta, *alpha, *ref, *prev;
+    double *bb, *gam, *beta, *alpha, *ref, *prev, *ss;  // ss: S^2 of the rounding floor
     int *act, *outer, *iters;
+    int* bad;  // a non-finite residual or right-hand side was seen (reported as MG_ENONFINITE)
     int* ctr;  // [0] iterations of the current PCG, [1] refinement sweep
 };
 
@@ -152,7 +158,7 @@ template <int MODE>
 __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restrict__ ca, double inv_dt,
                                                const double* __restrict__ F, double J0, double* x64, double* r64,
                                                double* p64, double* q64, double* b64, float* z, double* part_bb,
-                                               double* part_rr, float* r32s) {
+                                               double* part_rr, double* part_ss, float* r32s) {
     phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
@@ -166,10 +172,10 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
     const double* xprev = ca->xprev;
     const double* guess = ca->guess;
     const double* g = ca->g;
-    double bb[1] = {0.0}, rr[1] = {0.0};
+    double bb[1] = {0.0}, rr[1] = {0.0}, ss[1] = {0.0};
     const int i1 = min(D.n, (rb + 1) * D.rbs);
     for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
-        double bi = 0.0, lx = 0.0, xi = 0.0;
+        double bi = 0.0, lx = 0.0, xi = 0.0, alx = 0.0;
         if (valid) {
             double mb = 0.0;
             for (int w = 0; w < D.W; ++w) {
@@ -178,7 +184,9 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
                 if (guess) {
                     double xj = guess[j * ca->ld_guess + gc];
                     if (g) xj -= g[j * ca->ld_g + gc];
-                    lx += __ldg(D.L64 + w * D.n + i) * xj;
+                    const double a = __ldg(D.L64 + w * D.n + i);
+                    lx += a * xj;
+                    alx += fabs(a) * fabs(xj);
                 }
             }
             bi = mb * inv_dt + J0 * (sg[0] * F[i] + sg[1] * F[D.n + i] + sg[2] * F[2 * D.n + i]);
@@ -197,6 +205,8 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
             p64[o] = 0.0;
             q64[o] = 0.0;
             rr[0] += ri * ri;
+            const double si = fabs(bi) + alx;
+            ss[0] += si * si;
         } else {
             b64[o] = bi;
         }
@@ -206,6 +216,8 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
     if (MODE == 0) {
         __syncthreads();
         block_partial<1>(rr, part_rr);
+        __syncthreads();
+        block_partial<1>(ss, part_ss);
     }
 }
 
@@ -228,18 +240,24 @@ __global__ void __launch_bounds__(NTB) kb_final(Depth D, const CallArgs* __restr
 constexpr int NSB = 1024;
 
 // FP64 form: ||b||^2, ||r0||^2 -> active columns, loop condition.
-__global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* part_bb, const double* part_rr, int nrb,
-                                                      int kpad, const CallArgs* __restrict__ ca,
-                                                      cudaGraphConditionalHandle h, int use_cond) {
+// part_ss null: no rounding floor (Newton corrections start from delta = 0).
+__global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* part_bb, const double* part_rr,
+                                                      const double* part_ss, int nrb, int kpad,
+                                                      const CallArgs* __restrict__ ca, cudaGraphConditionalHandle h,
+                                                      int use_cond) {
     phase_begin();
     int any = 0;
     for (int c = threadIdx.x; c < kpad; c += NSB) {
         const double bb = col_total(part_bb, nrb, c), rr = col_total(part_rr, nrb, c);
+        const double ss = part_ss ? col_total(part_ss, nrb, c) : 0.0;
         st.bb[c] = bb;
         st.ref[c] = bb;
+        st.ss[c] = ss;
         st.gam[c] = 0.0;
         st.iters[c] = 0;
-        const int a = (c < ca->k) && !(rr <= ca->tol2 * bb);
+        st.bad[c] = (c < ca->k) && !(rr == rr && bb == bb && rr - rr == 0.0 && bb - bb == 0.0);
+        // a guess that already solves the step to working precision is kept as it is
+        const int a = (c < ca->k) && !(rr <= ca->tol2 * bb || rr <= ca->fl_acc2 * ss);
         st.act[c] = a;
         any |= a;
     }
@@ -258,10 +276,12 @@ __global__ void __launch_bounds__(NSB) kb_scalar_init1(Cols st, const double* pa
                                                       int use_cond) {
     phase_begin();
     for (int c = threadIdx.x; c < kpad; c += NSB) {
-        st.bb[c] = col_total(part_bb, nrb, c);
+        const double bb = col_total(part_bb, nrb, c);
+        st.bb[c] = bb;
         st.outer[c] = c < ca->k;
         st.iters[c] = 0;
         st.act[c] = 0;
+        st.bad[c] = (c < ca->k) && !(bb - bb == 0.0);
     }
     if (threadIdx.x == 0) {
         st.ctr[1] = 0;
@@ -325,7 +345,9 @@ __global__ void __launch_bounds__(NTB) kb_scalar_conv(Cols st, const double* par
         const double v = rr[threadIdx.x];
         if (st.act[c]) {
             st.iters[c] += 1;
-            if (v <= tol2 * st.ref[c] || !(v == v)) st.act[c] = 0;
+            const bool floor = !inner && v <= ca->fl_stop2 * st.ss[c];
+            if (!(v - v == 0.0)) st.bad[c] = 1;
+            if (v <= tol2 * st.ref[c] || floor || !(v - v == 0.0)) st.act[c] = 0;
         }
         any = st.act[c];
     }
@@ -346,8 +368,8 @@ __global__ void __launch_bounds__(NTB) kb_scalar_conv(Cols st, const double* par
 }
 
 // refinement decisions after r = b - L64 x; sets the inner and outer loop conditions
-__global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* part, int nrb, int kpad,
-                                                       const CallArgs* __restrict__ ca,
+__global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* part, const double* part_ss, int nrb,
+                                                       int kpad, const CallArgs* __restrict__ ca,
                                                        cudaGraphConditionalHandle h_inner,
                                                        cudaGraphConditionalHandle h_outer, int use_cond) {
     phase_begin();
@@ -356,10 +378,14 @@ __global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* p
     for (int c = threadIdx.x; c < kpad; c += NSB) {
         const double rr = col_total(part, nrb, c);
         if (st.outer[c] == 1) {
-            const bool met = rr <= ca->tol2 * st.bb[c];
+            // tolerance met, or x solves the step to working precision (the initial
+            // guess within the acceptance margin, a refined iterate at the floor itself)
+            const double fl2 = sweep == 0 ? ca->fl_acc2 : ca->fl_stop2;
+            const bool met = rr <= ca->tol2 * st.bb[c] || rr <= fl2 * col_total(part_ss, nrb, c);
             const bool stalled = sweep > 0 && rr > 0.25 * st.prev[c];
             if (met || (stalled && rr <= 1e-16 * st.bb[c])) st.outer[c] = 0;
-            else if (stalled || sweep >= ca->max_refine || !(rr == rr)) st.outer[c] = 2;
+            else if (stalled || sweep >= ca->max_refine || !(rr - rr == 0.0)) st.outer[c] = 2;
+            if (!(rr - rr == 0.0)) st.bad[c] = 1;
         }
         const int a = st.outer[c] == 1;
         st.act[c] = a;
@@ -385,21 +411,24 @@ __global__ void __launch_bounds__(NSB) kb_scalar_final(Cols st, int kpad, const 
     phase_begin();
     for (int c = threadIdx.x; c < kpad && c < ca->k; c += NSB) {
         const int failed = mode == 0 ? st.act[c] : st.outer[c] != 0;
-        if (failed) atomicMin(worst, (int)MG_ECG_MAXIT);
+        if (st.bad[c]) atomicMin(worst, (int)MG_ENONFINITE);
+        else if (failed) atomicMin(worst, (int)MG_ECG_MAXIT);
         atomicAdd(iter_sum, (unsigned long long)st.iters[c]);
     }
 }
 
 // Exact float -> double conversion with integer instructions: on GB300 the F2F
 // conversion issues on the FP64 pipe, whose rate is a small fraction of FP32's.
-// Normal numbers convert exactly; zero and denormals give (signed) zero, infinities
-// and NaNs are not produced by the preconditioner.
+// Normal numbers convert exactly; zero and denormals give (signed) zero; infinities
+// stay infinities and NaNs stay NaNs (exponent all ones maps to all ones, the
+// mantissa bits are kept), so a poisoned preconditioner output reaches the
+// convergence test instead of turning into a large finite number.
 __device__ __forceinline__ double f2d_int(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
     const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
     const unsigned long long mant = (unsigned long long)(u & 0x7fffffu) << 29;
-    const unsigned long long ex = (unsigned long long)(e + (1023u - 127u)) << 52;
+    const unsigned long long ex = (unsigned long long)(e == 0xffu ? 0x7ffu : e + (1023u - 127u)) << 52;
     return __longlong_as_double((long long)(e ? (sign | ex | mant) : sign));
 }
 
@@ -952,21 +981,24 @@ __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, c
 // FP32+refinement: r = b - L64 x for columns still refining (else 0); r32 = r, d = p = q = 0
 __global__ void __launch_bounds__(NTB) kb_refine_r(Depth D, const double* b64, const double* x64, float* r32,
                                                    float* d32, float* p32, float* q32, const int* outer,
-                                                   double* part) {
+                                                   double* part, double* part_ss) {
     phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
     const bool on = outer[gc] == 1;
-    double rr[1] = {0.0};
+    double rr[1] = {0.0}, ss[1] = {0.0};
     const double* x = tv(x64, D.n, t);
     const int i1 = min(D.n, (rb + 1) * D.rbs);
     for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
         double ri = 0.0;
         if (on) {
-            double lx[1];
-            ell_vec<G, 1, double>(D.col, D.L64, D.n, D.W, i, x, lc, lx);
-            ri = b64[((size_t)t * D.n + i) * G + lc] - lx[0];
+            double lx, alx;
+            ell_row_abs<G>(D.col, D.L64, D.n, D.W, i, x, lc, lx, alx);
+            const double bi = b64[((size_t)t * D.n + i) * G + lc];
+            ri = bi - lx;
+            const double si = fabs(bi) + alx;
+            ss[0] += si * si;
         }
         const size_t o = ((size_t)t * D.n + i) * G + lc;
         r32[o] = (float)ri;
@@ -976,6 +1008,8 @@ __global__ void __launch_bounds__(NTB) kb_refine_r(Depth D, const double* b64, c
         rr[0] += ri * ri;
     }
     block_partial<1>(rr, part);
+    __syncthreads();
+    block_partial<1>(ss, part_ss);
 }
 
 __global__ void __launch_bounds__(NTB) kb_update_x(Depth D, double* x64, const float* d32, const int* outer) {
@@ -1246,7 +1280,7 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             P->q32 = (float*)alloc(*P, e0 * 4);
         }
         const int kpad = ntile * G;
-        P->cols.ensure((size_t)kpad * (6 * sizeof(double) + 3 * sizeof(int)) + 64);
+        P->cols.ensure((size_t)kpad * (7 * sizeof(double) + 4 * sizeof(int)) + 64);
         char* cb = (char*)P->cols.p;
         P->st.bb = (double*)cb;
         P->st.gam = P->st.bb + kpad;
@@ -1254,12 +1288,14 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         P->st.alpha = P->st.beta + kpad;
         P->st.ref = P->st.alpha + kpad;
         P->st.prev = P->st.ref + kpad;
-        P->st.act = (int*)(P->st.prev + kpad);
+        P->st.ss = P->st.prev + kpad;
+        P->st.act = (int*)(P->st.ss + kpad);
         P->st.outer = P->st.act + kpad;
         P->st.iters = P->st.outer + kpad;
-        P->st.ctr = P->st.iters + kpad;
+        P->st.bad = P->st.iters + kpad;
+        P->st.ctr = P->st.bad + kpad;
         const int nrb0 = P->depth[0].nrb;
-        P->part.ensure((size_t)2 * ntile * std::max(nrb0, 1) * G * sizeof(double));
+        P->part.ensure((size_t)3 * ntile * std::max(nrb0, 1) * G * sizeof(double));
         P->args.ensure(sizeof(CallArgs));
         // ---- capture
         MG_CUDA(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
@@ -1272,6 +1308,7 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         Depth& D0 = P->depth[0];
         double* part = P->part.as<double>();
         double* part2 = part + (size_t)ntile * nrb0 * G;
+        double* part3 = part2 + (size_t)ntile * nrb0 * G;
         const double inv_dt = 1.0 / op.dt;
         const double J0 = c->pwm.J0;
         if (so.precision == MG_FP64) {
@@ -1281,8 +1318,9 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
                                                              D0.x, part, part2, P->r32s);
             else
                 kb_init<0><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, P->r64,
-                                                             P->p64, P->q64, nullptr, D0.x, part, part2, P->r32s);
-            kb_scalar_init0<<<1, NSB, 0, s>>>(P->st, part, part2, nrb0, kpad, ca, h, 1);
+                                                             P->p64, P->q64, nullptr, D0.x, part, part2, part3,
+                                                             P->r32s);
+            kb_scalar_init0<<<1, NSB, 0, s>>>(P->st, part, part2, P->pc ? nullptr : part3, nrb0, kpad, ca, h, 1);
             cudaGraph_t body = add_while(s, h);
             if (!P->pc) kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
             kb_scalar_final<<<1, NSB, 0, s>>>(P->st, kpad, ca, 0, (unsigned long long*)c->counters.p,
@@ -1294,7 +1332,8 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         } else {
             cudaGraphConditionalHandle ho = new_handle(s);
             kb_init<1><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, nullptr,
-                                                         nullptr, nullptr, P->b64, D0.x, part, part2, nullptr);
+                                                         nullptr, nullptr, P->b64, D0.x, part, part2, nullptr,
+                                                         nullptr);
             kb_scalar_init1<<<1, NSB, 0, s>>>(P->st, part, nrb0, kpad, ca, ho, 1);
             cudaGraph_t outer = add_while(s, ho);
             kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
@@ -1305,8 +1344,8 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             MG_CUDA(cudaStreamBeginCaptureToGraph(s2, outer, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
             cudaGraphConditionalHandle hi = new_handle(s2);
             kb_refine_r<<<grid(ntile, nrb0), NTB, 0, s2>>>(D0, P->b64, P->x64, P->r32, P->d32, P->p32, P->q32,
-                                                           P->st.outer, part);
-            kb_scalar_refine<<<1, NSB, 0, s2>>>(P->st, part, nrb0, kpad, ca, hi, ho, 1);
+                                                           P->st.outer, part, part3);
+            kb_scalar_refine<<<1, NSB, 0, s2>>>(P->st, part, part3, nrb0, kpad, ca, hi, ho, 1);
             cudaGraph_t inner = add_while(s2, hi);
             kb_update_x<<<grid(ntile, nrb0), NTB, 0, s2>>>(D0, P->x64, P->d32, P->st.outer);
             MG_CUDA(cudaStreamEndCapture(s2, &outer));
@@ -1342,10 +1381,11 @@ static void run_eager_fp64(mg_ctx* c, GraphPlan& P, int iters) {
     const int nrb0 = D0.nrb, kpad = P.ntile * G;
     double* part = P.part.as<double>();
     double* part2 = part + (size_t)P.ntile * nrb0 * G;
+    double* part3 = part2 + (size_t)P.ntile * nrb0 * G;
     const CallArgs* ca = P.args.as<CallArgs>();
     kb_init<0><<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, 1.0 / P.op->dt, m0.F.as<double>(), c->pwm.J0, P.x64, P.r64,
-                                                   P.p64, P.q64, nullptr, D0.x, part, part2, P.r32s);
-    kb_scalar_init0<<<1, NSB, 0, s>>>(P.st, part, part2, nrb0, kpad, ca, 0, 0);
+                                                   P.p64, P.q64, nullptr, D0.x, part, part2, part3, P.r32s);
+    kb_scalar_init0<<<1, NSB, 0, s>>>(P.st, part, part2, part3, nrb0, kpad, ca, 0, 0);
     for (int it = 0; it < iters; ++it)
         capture_pcg_body<double>(P, s, P.x64, P.r64, P.p64, P.q64, D0.L64, ca, 0, 0, 0);
     kb_final<<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, P.x64);
@@ -1390,6 +1430,9 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
     a.inner_tol2 = so.inner_tol * so.inner_tol;
     a.max_it = so.max_cg;
     a.max_refine = so.max_refine;
+    const double fs = residual_floor(P->depth[0].W);
+    a.fl_stop2 = fs * fs;
+    a.fl_acc2 = (kFloorAccept * fs) * (kFloorAccept * fs);
     MG_CUDA(cudaMemcpyAsync(P->args.p, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
     const char* eager = getenv("MGRIT_EM_EAGER");
     if (eager && so.precision == MG_FP64) run_eager_fp64(c, *P, atoi(eager));

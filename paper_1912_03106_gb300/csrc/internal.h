@@ -190,6 +190,27 @@ inline int smooth_sweeps(const mg_solver_opts& so) { return so.smooth > 0 ? so.s
 const int8_t* ctx_find_pwm_table(const mg_ctx* c, int64_t N, double T);
 const double* ctx_find_wave_table(const mg_ctx* c, int64_t N, double T, int kind);
 
+// Rounding floor of a step's FP64 residual.  One row of r = b - L x with W stored
+// entries is a sum of W + 1 products; its computed value differs from the exact one
+// by at most gamma_{W+1} (|b_i| + sum_j |L_ij| |x_j|), gamma_k = k u / (1 - k u),
+// u = 2^-53 (the standard bound for recursive summation of products).  A column
+// whose computed ||r|| is within a small multiple of gamma_{W+1} S,
+// S = || |b| + |L| |x| ||, solves its step to working precision: the PCG iteration
+// stops at gamma S, and an initial guess (or a refined iterate) is accepted as it is
+// up to kFloorAccept gamma S, which covers the gap between the recurrence residual
+// and the true residual that a finished solve leaves.  With the guess accepted,
+// re-solving a step from its own solution returns that solution bit for bit.
+inline double residual_floor(int W) {
+    const double u = 1.1102230246251565e-16;  // 2^-53
+    const double k = (double)(W + 1);
+    return k * u / (1.0 - k * u);
+}
+constexpr double kFloorAccept = 4.0;
+
+// Reject solver options outside their documented ranges (MG_EINVAL); every entry
+// point that runs a step calls it before any launch (mgrit.cu).
+void check_solver_opts(const mg_solver_opts& so);
+
 // ---- batched backward-Euler step (pcg.cu)
 struct PhiIO {
     int k = 0;

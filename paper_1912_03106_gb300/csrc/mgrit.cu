@@ -470,6 +470,8 @@ struct Solver {
     }
 };
 
+}  // namespace
+
 void check_solver_opts(const mg_solver_opts& so) {
     if (so.max_cg < 1 || so.max_refine < 0 || !(so.cg_tol >= 0.0) || !(so.refine_tol >= 0.0) ||
         !(so.inner_tol >= 0.0) || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) || so.cluster < 0 ||
@@ -484,12 +486,24 @@ void check_solver_opts(const mg_solver_opts& so) {
         mg_fail(MG_EINVAL, "bad solver options");
 }
 
+namespace {
+
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 void reset_counters(mg_ctx* c) {
     c->counters.ensure(16);
     int64_t init[2] = {0, 0};
     MG_CUDA(cudaMemcpyAsync(c->counters.p, init, 16, cudaMemcpyHostToDevice, c->stream));
+}
+
+const char* status_name(int st) {
+    switch (st) {
+        case MG_ECG_MAXIT: return "MG_ECG_MAXIT";
+        case MG_ENEWTON: return "MG_ENEWTON";
+        case MG_ETIMEOUT: return "MG_ETIMEOUT";
+        case MG_ENONFINITE: return "MG_ENONFINITE";
+        default: return "solver failure";
+    }
 }
 
 void fill_stats(mg_ctx* c, const SolveCounters& cnt, mg_stats* st) {
@@ -546,12 +560,16 @@ mg_status sequential_impl(mg_ctx* c, int level, int64_t N, double T, const doubl
         io.tstride = 0;
         phi_batch(c, op, io, so, &cnt);
     }
-    if (stats) {
-        fill_stats(c, cnt, stats);
-        auto t2 = clk::now();
-        stats->t_setup = secs(t0, t1);
-        stats->t_solve = secs(t1, t2);
-        if (stats->worst_status != 0) return (mg_status)stats->worst_status;
+    // the per-column statuses are read whether or not the caller wants statistics
+    mg_stats local;
+    std::memset(&local, 0, sizeof(local));
+    mg_stats* st = stats ? stats : &local;
+    fill_stats(c, cnt, st);
+    st->t_setup = secs(t0, t1);
+    st->t_solve = secs(t1, clk::now());
+    if (st->worst_status != 0) {
+        c->err = "mg_sequential: a step solve did not converge (" + std::string(status_name(st->worst_status)) + ")";
+        return (mg_status)st->worst_status;
     }
     return MG_OK;
 }
@@ -684,6 +702,16 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
         S.o.solver.refine_tol = std::max(tol_ref, o.step_tol_ratio * rho);
     };
     set_step_tol(1.0);
+    // stagnation (residual rule only): for kStallIters iterations in a row no residual
+    // below kStallDrop times the best one so far (slow but steady convergence, e.g.
+    // 0.95 per iteration, keeps making such progress; a residual that only wanders at
+    // a floor does not)
+    constexpr int kStallIters = 5;
+    constexpr double kStallDrop = 0.9;
+    double best = INFINITY;
+    int since_best = 0;
+    bool stalled = false;
+    double ref = 1.0;
     for (it = 0;; ++it) {
         S.relax(0);
         S.residual(0);
@@ -693,29 +721,50 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
             std::fprintf(stderr, "[mgrit] iteration %d  residual %.4e  %.3f s  step-solves %lld  newton %lld\n", it,
                          rn, secs(t1, clk::now()), (long long)S.cnt.step_solves, (long long)S.cnt.newton_iters);
         if (it == 0) r0 = rn;
-        double ref = (o.tol_relative && o.stop_rule == 0) ? r0 : 1.0;
+        ref = (o.tol_relative && o.stop_rule == 0) ? r0 : 1.0;
         if (rn <= o.tol * ref) {
             converged = true;
             break;
         }
         if (rn != rn || it >= o.max_iter) break;
+        if (o.stop_rule == 0) {
+            if (rn < kStallDrop * best || it == 0) {
+                best = std::min(best, rn);
+                since_best = 0;
+            } else if (++since_best >= kStallIters) {
+                stalled = true;
+                break;
+            }
+        }
         set_step_tol(r0 > 0.0 ? rn / r0 : 1.0);
         S.coarse_correction(0, o.cycle);
     }
     k_to_time_major<<<nblk(L0.n * (N + 1)), 256, 0, c->stream>>>(L0.n, N, L0.view(), out);
     S.cnt.launches += 1;
     MG_CUDA(cudaGetLastError());
-    if (stats) {
-        fill_stats(c, S.cnt, stats);
-        auto t2 = clk::now();
-        stats->iters = it;
-        stats->n_hist = (int)std::min<size_t>(hist.size(), 64);
-        for (int k = 0; k < stats->n_hist; ++k) stats->res_hist[k] = hist[k];
-        stats->t_setup = secs(t0, t1);
-        stats->t_solve = secs(t1, t2);
-        if (stats->worst_status != 0) return (mg_status)stats->worst_status;
+    // the per-column statuses are read whether or not the caller wants statistics
+    mg_stats local;
+    std::memset(&local, 0, sizeof(local));
+    mg_stats* st = stats ? stats : &local;
+    fill_stats(c, S.cnt, st);
+    st->iters = it;
+    st->n_hist = (int)std::min<size_t>(hist.size(), 64);
+    for (int k = 0; k < st->n_hist; ++k) st->res_hist[k] = hist[k];
+    st->t_setup = secs(t0, t1);
+    st->t_solve = secs(t1, clk::now());
+    if (st->worst_status != 0) {
+        c->err = "mg_solve: a step solve did not converge (" + std::string(status_name(st->worst_status)) + ")";
+        return (mg_status)st->worst_status;
     }
-    return converged ? MG_OK : MG_EMGRIT_MAXIT;
+    if (converged) return MG_OK;
+    char msg[256];
+    const double last = hist.empty() ? 0.0 : hist.back();
+    std::snprintf(msg, sizeof msg, "mg_solve: %s after %d iterations: %s %.3e (%.3e of the first), tolerance %.3e",
+                  stalled ? "residual stagnated" : (last != last ? "residual is not finite" : "max_iter reached"), it,
+                  o.stop_rule == 1 ? "Joule-loss change" : "residual", last, r0 > 0.0 ? last / r0 : 0.0,
+                  o.tol * ref);
+    c->err = msg;
+    return stalled ? MG_ESTALLED : MG_EMGRIT_MAXIT;
 }
 
 }  // namespace

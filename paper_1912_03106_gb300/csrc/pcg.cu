@@ -110,6 +110,7 @@ struct PcgArgs {
     float *d32, *r32, *p32, *q32;
     double tol;
     double inner_tol;
+    double fl_stop2, fl_acc2;  // rounding floor of the FP64 residual (squared factors of S, see internal.h)
     int max_it;
     int max_refine;
     int mode;
@@ -129,9 +130,11 @@ struct Smem {
     double alpha[KT];
     double ref[KT];
     double prev[KT];
+    double ss[KT];  // S^2 = || |b| + |L| |x| ||^2 of the rounding floor
     int act[KT];
     int outer[KT];
     int iters[KT];
+    int bad[KT];  // a non-finite residual or right-hand side was seen
     int any;
 };
 
@@ -639,10 +642,12 @@ struct PhPcgB {
 };
 
 // PCG on the tile for L d = r (tile-major depth-0 vectors of type T, operator Lv).
-// Columns with s.act set iterate; a column stops when ||r||^2 <= tol2 * s.ref.
+// Columns with s.act set iterate; a column stops when ||r||^2 <= tol2 * s.ref, or
+// at the rounding floor ||r||^2 <= fl_stop2 * s.ss; it does not start when its
+// initial residual is within fl_acc2 * s.ss (0, 0: no floor).
 template <int KT, class T>
 __device__ void pcg(Ctx<KT>& c, Smem<KT>& s, const PcgArgs& a, T* d, T* r, T* p, T* q, const T* Lv, double tol2,
-                    float* stage) {
+                    double fl_stop2, double fl_acc2, float* stage) {
     constexpr int VV = std::is_same<T, double>::value ? vd(KT) : vf(KT);
     constexpr int VF = vf(KT);
     const DepthArgs& D = a.d[0];
@@ -665,7 +670,12 @@ __device__ void pcg(Ctx<KT>& c, Smem<KT>& s, const PcgArgs& a, T* d, T* r, T* p,
         cluster_sum<KT, VV, 1, double>(c, s, v);
         if (threadIdx.x < KT) {
             int cc = threadIdx.x;
-            if (s.act[cc] && s.tot[0][cc] <= tol2 * s.ref[cc]) s.act[cc] = 0;
+            const double rr0 = s.tot[0][cc];
+            if (s.act[cc] && !(rr0 - rr0 == 0.0)) {
+                s.bad[cc] = 1;
+                s.act[cc] = 0;
+            }
+            if (s.act[cc] && (rr0 <= tol2 * s.ref[cc] || rr0 <= fl_acc2 * s.ss[cc])) s.act[cc] = 0;
             s.iters[cc] = 0;
             s.beta[cc] = 0.0;
         }
@@ -713,7 +723,8 @@ __device__ void pcg(Ctx<KT>& c, Smem<KT>& s, const PcgArgs& a, T* d, T* r, T* p,
                 if (s.act[cc]) {
                     s.iters[cc] = it;
                     double rr = s.tot[0][cc];
-                    if (rr <= tol2 * s.ref[cc] || !(rr == rr)) s.act[cc] = 0;
+                    if (!(rr - rr == 0.0)) s.bad[cc] = 1;
+                    if (rr <= tol2 * s.ref[cc] || rr <= fl_stop2 * s.ss[cc] || !(rr - rr == 0.0)) s.act[cc] = 0;
                 }
             }
             update_any(s);
@@ -747,6 +758,7 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
         s.act[threadIdx.x] = threadIdx.x < kc;
         s.outer[threadIdx.x] = threadIdx.x < kc;
         s.iters[threadIdx.x] = 0;
+        s.bad[threadIdx.x] = 0;
         s.gam[threadIdx.x] = 0.0;
     }
     __syncthreads();
@@ -755,12 +767,12 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
     // ---- b = (1/dt) M x_prev + J0 sum_s b_s F_s, x0 = guess - g; FP64 form: r = b - L x0.
     // Every column of the tile is initialised (columns past k with zeros).
     {
-        double v[1][1] = {{0.0}};
+        double v[2][1] = {{0.0}, {0.0}};  // ||b||^2 and, FP64 form, S^2 of the rounding floor
         double* r64 = a.mode == 0 ? c.tv(a.r64, D.n) : nullptr;
         double* b64 = a.mode == 1 ? c.tv(a.b64, D.n) : nullptr;
         float* z = c.tv(D.x, D.n);
         for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
-            double bi = 0.0, lx = 0.0, xi = 0.0;
+            double bi = 0.0, lx = 0.0, xi = 0.0, alx = 0.0;
             if (valid) {
                 double mb = 0.0;
                 for (int wq = 0; wq < D.W; ++wq) {
@@ -769,7 +781,9 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
                     if (a.guess) {
                         double xj = a.guess[j * a.ld_guess + cio];
                         if (a.g) xj -= a.g[j * a.ld_g + cio];
-                        lx += __ldg(D.L64 + (int64_t)wq * D.n + i) * xj;
+                        const double lv = __ldg(D.L64 + (int64_t)wq * D.n + i);
+                        lx += lv * xj;
+                        alx += fabs(lv) * fabs(xj);
                     }
                 }
                 bi = mb * a.inv_dt + a.J0 * (sg[0] * a.F[i] + sg[1] * a.F[D.n + i] + sg[2] * a.F[2 * D.n + i]);
@@ -789,16 +803,21 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
                 stcg(b64 + o, bi);
             }
             v[0][0] += bi * bi;
+            const double si = fabs(bi) + alx;
+            v[1][0] += si * si;
         }
-        cluster_sum<KT, 1, 1, double>(c, s, v);
-        if (threadIdx.x < KT) s.bb[threadIdx.x] = s.tot[0][threadIdx.x];
+        cluster_sum<KT, 1, 2, double>(c, s, v);
+        if (threadIdx.x < KT) {
+            s.bb[threadIdx.x] = s.tot[0][threadIdx.x];
+            s.ss[threadIdx.x] = s.tot[1][threadIdx.x];
+        }
         __syncthreads();
     }
 
     if constexpr (MODE == 0) {
         if (threadIdx.x < KT) s.ref[threadIdx.x] = s.bb[threadIdx.x];
         __syncthreads();
-        pcg<KT, double>(c, s, a, a.x64, a.r64, a.p64, a.q64, D.L64, a.tol * a.tol, stage);
+        pcg<KT, double>(c, s, a, a.x64, a.r64, a.p64, a.q64, D.L64, a.tol * a.tol, a.fl_stop2, a.fl_acc2, stage);
         if (threadIdx.x < KT) s.outer[threadIdx.x] = s.act[threadIdx.x];
         __syncthreads();
     } else {
@@ -809,14 +828,17 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
         float* p32 = c.tv(a.p32, D.n);
         float* q32 = c.tv(a.q32, D.n);
         for (int sweep = 0; sweep <= a.max_refine; ++sweep) {
-            // ---- r = b - L64 x (FP64); inner start d = 0, r32 = r
-            double v[1][1] = {{0.0}};
+            // ---- r = b - L64 x (FP64) and S^2 of its rounding floor; inner start d = 0, r32 = r
+            double v[2][1] = {{0.0}, {0.0}};
             for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
                 double ri = 0.0;
                 if (s.outer[lc] == 1) {
-                    double lx[1];
-                    ell_vec<KT, 1, double>(D.col, D.L64, D.n, D.W, i, (const double*)x64, lc, lx);
-                    ri = ldcg(b64 + i * KT + lc) - lx[0];
+                    double lx, alx;
+                    ell_row_abs<KT>(D.col, D.L64, D.n, D.W, (int)i, (const double*)x64, lc, lx, alx);
+                    const double bi = ldcg(b64 + i * KT + lc);
+                    ri = bi - lx;
+                    const double si = fabs(bi) + alx;
+                    v[1][0] += si * si;
                 }
                 const int64_t o = i * KT + lc;
                 stcg(r32 + o, (float)ri);
@@ -825,17 +847,19 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
                 stcg(q32 + o, 0.0f);
                 v[0][0] += ri * ri;
             }
-            cluster_sum<KT, 1, 1, double>(c, s, v);
+            cluster_sum<KT, 1, 2, double>(c, s, v);
             if (threadIdx.x < KT) {
                 int cc = threadIdx.x;
                 double rr = s.tot[0][cc];
                 if (s.outer[cc] == 1) {
-                    // done: tolerance met, or the FP64 residual no longer halves (rounding
-                    // floor of b - L x), accepted once it is below 1e-8 ||b||
-                    const bool met = rr <= a.tol * a.tol * s.bb[cc];
+                    // done: tolerance met or x solves the step to working precision, or the
+                    // FP64 residual no longer halves, accepted once it is below 1e-8 ||b||
+                    const double fl2 = sweep == 0 ? a.fl_acc2 : a.fl_stop2;
+                    const bool met = rr <= a.tol * a.tol * s.bb[cc] || rr <= fl2 * s.tot[1][cc];
                     const bool stalled = sweep > 0 && rr > 0.25 * s.prev[cc];
                     if (met || (stalled && rr <= 1e-16 * s.bb[cc])) s.outer[cc] = 0;
-                    else if (stalled || sweep == a.max_refine || !(rr == rr)) s.outer[cc] = 2;
+                    else if (stalled || sweep == a.max_refine || !(rr - rr == 0.0)) s.outer[cc] = 2;
+                    if (!(rr - rr == 0.0)) s.bad[cc] = 1;
                 }
                 s.act[cc] = s.outer[cc] == 1;
                 s.ref[cc] = rr;
@@ -843,7 +867,7 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
             }
             update_any(s);
             if (!s.any) break;
-            pcg<KT, float>(c, s, a, a.d32, a.r32, a.p32, a.q32, D.L32, a.inner_tol * a.inner_tol, stage);
+            pcg<KT, float>(c, s, a, a.d32, a.r32, a.p32, a.q32, D.L32, a.inner_tol * a.inner_tol, 0.0, 0.0, stage);
             if (threadIdx.x == 0) {
                 int mx = 0;
                 for (int cc = 0; cc < KT; ++cc) mx = max(mx, s.iters[cc]);
@@ -870,7 +894,8 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
     }
     if (c.rank == 0 && threadIdx.x < kc) {
         int cc = threadIdx.x;
-        if (s.outer[cc]) atomicMin(a.worst, (int)MG_ECG_MAXIT);
+        if (s.bad[cc]) atomicMin(a.worst, (int)MG_ENONFINITE);
+        else if (s.outer[cc]) atomicMin(a.worst, (int)MG_ECG_MAXIT);
         atomicAdd(a.iter_sum, (unsigned long long)(a.mode == 0 ? s.iters[cc] : (cc == 0 ? s.iters[0] : 0)));
     }
 }
@@ -1050,6 +1075,8 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
     a.k = io.k;
     a.tol = so.precision == MG_FP64 ? so.cg_tol : so.refine_tol;
     a.inner_tol = so.inner_tol;
+    a.fl_stop2 = residual_floor(a.d[0].W) * residual_floor(a.d[0].W);
+    a.fl_acc2 = a.fl_stop2 * kFloorAccept * kFloorAccept;
     a.max_it = so.max_cg;
     a.max_refine = so.max_refine;
     a.mode = so.precision == MG_FP64 ? 0 : 1;
@@ -1132,10 +1159,7 @@ void static_step(void* arg) {
         !q.x_in || !q.x_out || q.ld_in < q.k || q.ld_out < q.k || q.i0 < 0 || q.i0 > q.N || q.istride < 0 ||
         q.i0 + (int64_t)(q.k - 1) * q.istride > q.N)
         mg_fail(MG_EINVAL, "mg_step_static: bad arguments");
-    if (so.max_cg < 1 || so.max_refine < 0 || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) ||
-        (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID) || so.cluster < 0 || so.cluster > 16 ||
-        !(so.tile == 0 || so.tile == 1 || so.tile == 8 || so.tile == 16 || so.tile == 32))
-        mg_fail(MG_EINVAL, "mg_step_static: bad solver options");
+    check_solver_opts(so);
     const double dt = (double)q.dt_mult * q.T / (double)q.N;
     const StepOp* op = ctx_find_step_op(c, q.level, dt);
     const double* wave = ctx_find_wave_table(c, q.N, q.T, 0);
@@ -1244,6 +1268,8 @@ void static_step(void* arg) {
     a.k = q.k;
     a.tol = so.precision == MG_FP64 ? so.cg_tol : so.refine_tol;
     a.inner_tol = so.inner_tol;
+    a.fl_stop2 = residual_floor(a.d[0].W) * residual_floor(a.d[0].W);
+    a.fl_acc2 = a.fl_stop2 * kFloorAccept * kFloorAccept;
     a.max_it = so.max_cg;
     a.max_refine = so.max_refine;
     a.mode = so.precision == MG_FP64 ? 0 : 1;

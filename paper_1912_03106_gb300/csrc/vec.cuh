@@ -106,4 +106,19 @@ __device__ __forceinline__ void ell_vec(const int32_t* __restrict__ col, const V
     }
 }
 
+// One row of the FP64 residual product with the magnitude sum needed for its
+// rounding bound: acc = sum_w val[w, i] v[col[w, i]][c], aacc = sum_w |val| |v|.
+template <int KT>
+__device__ __forceinline__ void ell_row_abs(const int32_t* __restrict__ col, const double* __restrict__ val, int n,
+                                            int W, int i, const double* v, int c, double& acc, double& aacc) {
+    acc = 0.0;
+    aacc = 0.0;
+    for (int w = 0; w < W; ++w) {
+        const double a = __ldg(val + w * n + i);
+        const double x = __ldcg(v + (int64_t)__ldg(col + w * n + i) * KT + c);
+        acc += a * x;
+        aacc += fabs(a) * fabs(x);
+    }
+}
+
 }  // namespace mgv

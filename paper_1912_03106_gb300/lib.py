@@ -25,6 +25,8 @@ STATUS = {
     -7: "MG_EMGRIT_MAXIT",
     -8: "MG_ETIMEOUT",
     -9: "MG_ESTATE",
+    -10: "MG_ESTALLED",
+    -11: "MG_ENONFINITE",
 }
 
 MG_FP64 = 0

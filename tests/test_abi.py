@@ -144,3 +144,17 @@ def test_choose_levels_heuristic():
     assert m[0] == 4 and 64 // 4 // (2 ** (levels - 2)) >= 2
     with pytest.raises(api.L.MgError):
         api.mg_choose_levels([16], [1.0], 63)
+
+
+def test_choose_levels_reproduces_the_worked_example():
+    """Sec. 4.1's example: a fine grid of 129 points, 16 processors and five levels
+    give a first coarsening factor of 8 (16 intervals on the second level, eight
+    points per processor) and factor 2 below, down to a coarsest grid of 3 points.
+    Translated to one GPU, the processors are the batch width at which a batched
+    step stops gaining throughput: step times growing linearly from 16 columns on
+    make that width 16."""
+    from paper_1912_03106_gb300 import api
+
+    levels, m = api.mg_choose_levels([16, 32, 64], [1.0, 2.0, 4.0], 128, max_levels=5)
+    assert levels == 5 and m == [8, 2, 2, 2]
+    assert 128 // 8 // 2 // 2 // 2 + 1 == 3  # points on the coarsest grid

@@ -194,9 +194,9 @@ def run_mgrit(ctx, N, T, n, opts):
 
 @pytest.mark.parametrize("relax", [0, 1])
 def test_two_level_cfg0_matches_sequential_oracle(meshes, lin5k, relax):
-    """2-level MGRIT at the 24 x 48 mesh, N = 256, m = 16 (F and FCF).  The stop is
-    absolute (1e-11): the GPU's residual has a floor near 2e-13 from the 1e-13
-    step-solve tolerance, above 1e-11 relative to FCF's small first residual."""
+    """2-level MGRIT at the 24 x 48 mesh, N = 256, m = 16 (F and FCF), stopped at
+    the absolute residual 1e-11, with the residual history of the first
+    iterations as the oracle's."""
     model, ctx, ids = lin5k
     N, T = 256, 5e-3
     P = MachineProblem(meshes, model, N, T, (0, 0), (16,))

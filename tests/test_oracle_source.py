@@ -85,3 +85,33 @@ def test_joule_stop_rule_semantics(mesh0):
     assert hist[0] == float("inf")
     assert hist[-1] <= 1e-2
     assert all(h > 1e-2 for h in hist[:-1])
+
+
+@pytest.mark.parametrize("m", [(8,), (4, 2)])
+def test_joule_change_of_rescaled_rates(mesh0, m):
+    """Sec. 5.1's stopping quantity on trajectories with known losses.  The old
+    trajectory moves at a constant rate v, so P_i = P = v^T M_sigma v at every
+    step; the new one moves at s_i v in step i, so P_i(new) = s_i^2 P.  At the
+    finest C-points (multiples of m_0) the change is |s^2 - 1| / s^2, which tells
+    apart the reading it states (relative to the new losses) from dividing by the
+    old losses; the F-points carry a larger change (s = 3) that must not count."""
+    model = machine_model(pwm=PwmSpec(J0=1e6, f_carrier=5e3))
+    N, T = 32, 1e-3
+    P = MachineProblem(mesh0, model, N, T, (0,) * (len(m) + 1), m)
+    v = np.random.default_rng(5).standard_normal(P.n)
+    dt = T / N
+    m0 = m[0]
+    s = np.full(N + 1, 3.0)
+    c_scale = [1.1, 0.8, 1.3, 1.05, 0.95, 1.2, 0.9, 1.15]
+    for c in range(1, N // m0 + 1):
+        s[c * m0] = c_scale[c - 1]
+    s[0] = 1.0
+    u_old = np.outer(np.arange(N + 1) * dt, v)
+    u_new = np.cumsum(np.outer(s * dt, v), axis=0)
+    u_new -= u_new[0]  # u_0 = 0; step i moves by s_i dt v
+    want = max(abs(s[c] ** 2 - 1) / s[c] ** 2 for c in range(m0, N + 1, m0))
+    got = P.joule_change(u_old, u_new)
+    assert abs(got - want) <= 1e-12 * want, (got, want)
+    # the other readings give other values, so the pin separates them
+    assert abs(max(abs(s[c] ** 2 - 1) for c in range(m0, N + 1, m0)) - want) > 0.05
+    assert abs((3.0 ** 2 - 1) / 3.0 ** 2 - want) > 0.05

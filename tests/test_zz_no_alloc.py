@@ -66,3 +66,11 @@ def test_static_step_refuses_what_it_cannot_do(setup):
     with pytest.raises(api.L.MgError) as e:
         ctx.mg_step_static(ids[1], 4096, 5e-3, big, big.clone(), dt_mult=1, i0=0, istride=1)
     assert e.value.status == -1 and "static array" in str(e.value)
+    # solver options outside their ranges are refused before anything is launched,
+    # as by mg_step (9 sweeps exceed the 8 the smoothing weights have room for)
+    for bad in (dict(smooth=9), dict(smoother=2), dict(cheb_ratio=1.0), dict(omega=2.0), dict(path=3),
+                dict(rows_per_block=8)):
+        with pytest.raises(api.L.MgError) as e:
+            ctx.mg_step_static(ids[1], 4096, 5e-3, x, x.clone(), dt_mult=1, i0=1, istride=1,
+                               solver=api.solver_opts(**bad))
+        assert e.value.status == -1, bad
