@@ -1,23 +1,30 @@
 #!/usr/bin/env python3
-"""Benchmark: GB300 MGRIT on the PWM-driven annular machine, 18,240-DOF mesh, N = 4096.
+"""Benchmark: GB300 MGRIT on the PWM-driven annular machine.
 
-Workload (one "step" of this benchmark = one complete MGRIT solve to tolerance):
-  fine mesh: the 24 x 48 annulus refined twice (18,240 interior DOFs), linear
-  materials, three-phase triangle-carrier PWM at 20 kHz, J0 = 1e6 A/m^2,
-  T = 20 ms, N = 4096 backward-Euler steps; 3-level MGRIT, m = 16, FCF relaxation,
-  coarse time levels on the 1,104-DOF base mesh (direct spatial coarsening),
-  FP64 arithmetic form.  The MGRIT tolerance is chosen so that the maximal
-  relative L2 error per time point against GPU sequential stepping is <= 1e-6;
-  the error reached is reported.
+Default workload (cfg1; one "step" of this benchmark = one complete MGRIT solve
+to tolerance): fine mesh the 24 x 48 annulus refined twice (18,240 interior
+DOFs), linear materials, three-phase triangle-carrier PWM at 20 kHz,
+J0 = 1e6 A/m^2, T = 20 ms, N = 4096 backward-Euler steps; 3-level MGRIT, m = 16,
+FCF relaxation, coarse time levels on the 1,104-DOF base mesh (direct spatial
+coarsening), FP64 arithmetic form.  The MGRIT tolerance is chosen so that the
+maximal relative L2 error per time point against GPU sequential stepping is
+<= 1e-6; the error reached is reported.
+
+--workload picks another of the synthetic workloads (one JSON line each, same
+keys): cfg0 (1,104 DOFs, N = 256, 2-level F-relaxation), cfg2 (73,344 DOFs,
+N = 16,384; the FP32+FP64-refinement form timed beside the FP64 form), cfg3
+(18,240 DOFs with the Brauer law, J0 = 3e6, N = 8,192, Newton steps).
 
 value = fine time steps resolved per second of MGRIT wall time (N / t_MGRIT),
 summed over ranks (independent replicas, one per GPU).  Also reported: GPU
 sequential stepping wall time on the same GB300 and the speedup, the live
-roofline of the dominant kernel (the batched step solve at 18,240 DOFs x 256
-columns), end-to-end throughput through the host-buffer entry point, sampled
-clocks, and the CPU oracle's sequential stepping on a bounded sample.
+roofline of the dominant kernel (the level-0 batched step solve), end-to-end
+throughput through the host-buffer entry point, sampled clocks, the error
+against the CPU oracle on the leading time points, and the CPU oracle's
+sequential stepping on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload cfg0|cfg1|cfg2|cfg3]
 """
 
 from __future__ import annotations
@@ -40,6 +47,25 @@ METRIC = "MGRIT wall time vs GPU sequential stepping at <=1e-6 rel err; SpMM/CG 
 UNIT = "time-steps/s"
 WORKLOAD = "cfg1: 18,240-DOF annulus, N=4096, T=20 ms, 3-level MGRIT m=16 FCF, coarse levels on 1,104 DOFs"
 N_STEPS, T_END, F_CARRIER = 4096, 20e-3, 20e3
+# the workloads --workload selects: (synth.workloads name, description, leading time
+# points the CPU oracle computes for the error check)
+BENCH_WORKLOADS = {
+    "cfg0": ("cfg0_linear_l0_N256",
+             "cfg0: 1,104-DOF annulus, N=256, T=5 ms, 5 kHz PWM, 2-level MGRIT m=16 F-relaxation", 256),
+    "cfg1": ("cfg1_linear_l2_N4096", WORKLOAD, 4096),
+    "cfg2": ("cfg2_mixed_l3_N16384",
+             "cfg2: 73,344-DOF annulus, N=16384, T=20 ms, 3-level MGRIT m=16 FCF, coarse levels on 1,104 DOFs, "
+             "FP32+FP64-refinement form (FP64 form timed beside it)", 256),
+    "cfg3": ("cfg3_nonlinear_l2_N8192",
+             "cfg3: 18,240-DOF annulus, Brauer law, J0=3e6, N=8192, T=20 ms, 3-level MGRIT m=16 FCF, "
+             "coarse levels on 1,104 DOFs, Newton to 1e-8", 0),
+}
+# cfg3: sequential Newton stepping is timed on this many leading steps and its
+# time extrapolated to N (a full run takes about half an hour); they are also the
+# error reference.  The MGRIT tolerance is fixed (a calibration ladder of full
+# nonlinear solves would take too long) and nested iterations give the first guess.
+NONLINEAR_SEQ_PREFIX = 128
+NONLINEAR_TOL = 1e-7
 ERR_TARGET = 1e-6   # metric: maximal relative L2 error per time point vs sequential stepping
 ERR_MARGIN = 0.5    # calibrate to half the target
 TOL_LADDER = (1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7, 1e-8)
@@ -96,9 +122,17 @@ def parse():
     ap.add_argument("--path", type=int, default=0, help="with --profile-step: 0 auto, 1 cluster, 2 graph")
     ap.add_argument("--reps", type=int, default=2, help="with --profile-step: number of steps")
     ap.add_argument("--level", type=int, default=2, help="with --profile-step: mesh level 0..3 (18,240 DOFs = 2)")
+    ap.add_argument("--tol", type=float, default=0.0,
+                    help="with --profile-step: step tolerance (cg_tol and refine_tol; 0: library default)")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default launch shapes")
     ap.add_argument("--instances", type=int, default=0, metavar="M",
                     help="only the batching workload: M uneven instances, concurrent vs one by one")
+    ap.add_argument("--workload", default="cfg1", choices=sorted(BENCH_WORKLOADS),
+                    help="synthetic workload (default cfg1, the headline)")
+    ap.add_argument("--oracle-points", type=int, default=-1,
+                    help="leading time points checked against the CPU oracle (-1: the workload's default)")
+    ap.add_argument("--no-sc", action="store_true",
+                    help="every MGRIT level on the fine mesh (no spatial coarsening)")
     return ap.parse_args()
 
 
@@ -130,6 +164,8 @@ def profile_step(args):
     k = args.profile_step
     x_in, out = step_inputs(ctx, ids, k, args.level)
     so = api.solver_opts(precision=args.precision, path=args.path)
+    if args.tol > 0.0:
+        so.cg_tol = so.refine_tol = args.tol
 
     def step():
         return ctx.mg_step(ids[args.level], N_STEPS, T_END, x_in, out, i0=1, istride=1 if k > 1 else 0,
@@ -151,18 +187,22 @@ def profile_step(args):
     kb = 8 if args.precision == 0 else 4
     per_col = step_bytes_per_column_iteration(ns, nu=so.smooth, krylov_bytes=kb)
     alg = it_col * (k * per_col + matrix_bytes_per_iteration(ns, nu=so.smooth)) + k * ns[0] * 8 * 9
+    survey = survey_bytes_per_unit(args.precision) * ns[0] * k * it_col
     print(json.dumps({"profile_step": k, "level": args.level, "dofs": ns[0], "precision": args.precision,
-                      "ms": ms, "pcg_iters_per_column": it_col, "algorithmic_bytes": alg,
-                      "algorithmic_gbs": alg / ms / 1e6}))
+                      "tol": so.cg_tol if args.precision == 0 else so.refine_tol,
+                      "ms": ms, "pcg_iters_per_column": it_col, "survey_bytes": survey,
+                      "survey_gbs": survey / ms / 1e6, "all_pass_bytes": alg, "all_pass_gbs": alg / ms / 1e6}))
 
 
 def instances_run(args):
     """The batching workload: M seeded uneven machine instances (meshes of 1,104 /
-    4,512 / 18,240 DOFs, N of 256 / 512 / 1,024 steps over 5 ms, 5/10/20 kHz
-    carriers, J0 in [0.5e6, 3e6], half of the 1,104-DOF ones with the Brauer law),
-    each a 2-level FCF MGRIT solve (m = 16, tolerance 1e-6, FP32+refinement for
-    linear instances, FP64 Newton for nonlinear ones), solved concurrently by
-    mg_batch_solve and one by one; aggregate step-solves per second of both."""
+    4,512 / 18,240 / 73,344 DOFs, N of 1,024 / 4,096 / 16,384 steps over 20 ms,
+    5/10/20 kHz carriers, J0 uniform in [0.5e6, 3e6] A/m^2, half of the
+    1,104-DOF ones with the Brauer law), each a 3-level FCF MGRIT solve (m = 16
+    on its own mesh, relative tolerance 1e-7 with inexact step solves; linear
+    instances in the FP32+refinement form, Brauer-law instances with FP64 Newton
+    steps), solved concurrently by mg_batch_solve and one by one; aggregate
+    step-solves per second of both."""
     import torch
 
     import synth
@@ -170,8 +210,8 @@ def instances_run(args):
     from synth.workloads import instances
     from paper_1912_03106_gb300 import api
 
-    meshes = synth.mesh_hierarchy(3)
-    insts = instances(args.instances, seed=0, mesh_levels=(0, 1, 2), Ns=(256, 512, 1024), T=5.0e-3,
+    meshes = synth.mesh_hierarchy(4)
+    insts = instances(args.instances, seed=0, mesh_levels=(0, 1, 2, 3), Ns=(1024, 4096, 16384), T=20.0e-3,
                       nonlinear_fraction=0.5, nonlinear_levels=(0,))
     setups = []
     for inst in insts:
@@ -180,39 +220,48 @@ def instances_run(args):
         ids = api.setup_machine(ctx, meshes[:inst.mesh_level + 1], model)
         lv = ids[inst.mesh_level]
         n = ctx.mg_num_dofs(lv)
-        opts = api.mgrit_opts(levels=2, m=(16,), space_level=(lv, lv), relax=1, tol=1e-6, max_iter=30,
+        opts = api.mgrit_opts(levels=3, m=(16, 16), space_level=(lv, lv, lv), relax=1, tol=1e-7, max_iter=40,
+                              step_tol_ratio=STEP_TOL_RATIO, nested=inst.nonlinear,
                               solver=api.solver_opts(precision=0 if inst.nonlinear else 1))
         setups.append((ctx, opts, torch.zeros(n, dtype=torch.float64, device="cuda"),
                        torch.zeros((inst.N + 1, n), dtype=torch.float64, device="cuda")))
     torch.cuda.synchronize()
-    args_b = ([s[0] for s in setups], [i.N for i in insts], [i.T for i in insts], [s[2] for s in setups],
-              [s[3] for s in setups], [s[1] for s in setups])
+    args_b = ([s_[0] for s_ in setups], [i.N for i in insts], [i.T for i in insts], [s_[2] for s_ in setups],
+              [s_[3] for s_ in setups], [s_[1] for s_ in setups])
     api.mg_batch_solve(*args_b)  # warm-up: plans, step operators, PWM tables
     t0 = time.perf_counter()
     rc, status, stats = api.mg_batch_solve(*args_b)
     t_conc = time.perf_counter() - t0
-    solves = sum(s["step_solves"] for s in stats)
+    solves = sum(s_["step_solves"] for s_ in stats)
     t0 = time.perf_counter()
     for (ctx, opts, a0, out), inst in zip(setups, insts):
-        ctx.mg_solve(inst.N, inst.T, a0, out, opts, allow=(-7,))
+        ctx.mg_solve(inst.N, inst.T, a0, out, opts, allow=(-7, -10))
         torch.cuda.current_stream().wait_stream(ctx.stream)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    print(json.dumps({"instances": len(insts), "status": rc,
-                      "mix": {"dofs": [s[2].numel() for s in setups], "N": [i.N for i in insts],
+    print(json.dumps({"instances": len(insts), "status": rc, "statuses": sorted(set(status)),
+                      "mix": {"dofs": [s_[2].numel() for s_ in setups], "N": [i.N for i in insts],
                               "nonlinear": [i.nonlinear for i in insts]},
                       "step_solves": solves, "concurrent_s": t_conc, "one_by_one_s": t_seq,
                       "concurrent_step_solves_per_s": solves / t_conc, "one_by_one_step_solves_per_s": solves / t_seq,
-                      "speedup": t_seq / t_conc}))
-    for s in setups:
-        s[0].close()
+                      "speedup": t_seq / t_conc, "iters": [s_["iters"] for s_ in stats]}))
+    for s_ in setups:
+        s_[0].close()
 
 
-def workload_config(n_fine, n_coarse, world):
+def workload_config(n_fine, n_coarse, world, key="cfg1"):
     """The workload keys both arms report (the MGRIT arm adds its solver settings)."""
-    return {"workload": WORKLOAD, "dofs": n_fine, "N": N_STEPS, "T_s": T_END, "levels": 3, "m": [16, 16],
-            "relax": "FCF", "space_levels": [n_fine, n_coarse, n_coarse], "error_target": ERR_TARGET,
-            "l2_flush": "inputs larger than L2 (600 MB trajectory per solve)", "parallelism": f"replicas x{world}"}
+    from synth.workloads import workload
+
+    w = workload(BENCH_WORKLOADS[key][0])
+    traj_mb = (w.N + 1) * n_fine * 8 / 1e6
+    return {"workload": BENCH_WORKLOADS[key][1], "dofs": n_fine, "N": w.N, "T_s": w.T, "levels": w.levels,
+            "m": list(w.m), "relax": "FCF" if w.relax else "F",
+            "space_levels": [n_fine if s_ == w.fine_level else n_coarse for s_ in w.space_levels],
+            "error_target": ERR_TARGET,
+            "l2_flush": ("inputs larger than L2 (%.0f MB trajectory per solve)" % traj_mb) if traj_mb > 129 else
+                        ("trajectory of %.0f MB fits the 129 MB L2: no flush between solves, L2-resident" % traj_mb),
+            "parallelism": f"replicas x{world}"}
 
 
 def max_over_ranks(t, world, device):
@@ -326,12 +375,35 @@ def matrix_bytes_per_iteration(ns, W=7, nu=5):
 
 
 # ---------------------------------------------------------------- our arm
-def run_ours(args, rank, world, local):
-    import numpy as np
+def survey_bytes_per_unit(precision):
+    """Algorithmic bytes of one unknown x column x PCG iteration in the survey's
+    unit (fused PCG iteration: ~9 vector passes of 8 B, plus the ELL matrix over a
+    32-column tile): 76 B in the FP64 form, 38 B with FP32 Krylov vectors."""
+    return 76.0 if precision == 0 else 38.0
+
+
+def workload_setup(key, local):
+    """Context, mesh ids and MGRIT options of a bench workload (synth.workloads)."""
     import torch
 
     import synth
     from synth.model import PwmSpec, machine_model
+    from synth.workloads import workload
+    from paper_1912_03106_gb300 import api
+
+    w = workload(BENCH_WORKLOADS[key][0])
+    meshes = synth.mesh_hierarchy(w.fine_level + 1)
+    model = machine_model(nonlinear=w.nonlinear, pwm=PwmSpec(J0=w.J0, f_carrier=w.f_carrier))
+    stream = torch.cuda.current_stream(local)
+    ctx = api.Context(local, stream)
+    ids = api.setup_machine(ctx, meshes, model)
+    return w, meshes, model, ctx, ids, stream
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
     from paper_1912_03106_gb300 import api
 
     torch.cuda.set_device(local)
@@ -340,26 +412,32 @@ def run_ours(args, rank, world, local):
         import torch.distributed as td
 
         td.init_process_group("nccl", device_id=dev)
-    meshes = synth.mesh_hierarchy(3)
-    model = machine_model(pwm=PwmSpec(J0=1e6, f_carrier=F_CARRIER))
-    stream = torch.cuda.current_stream(local)
-    ctx = api.Context(local, stream)
-    ids = api.setup_machine(ctx, meshes, model)
-    n = ctx.mg_num_dofs(ids[2])
-    N, T = N_STEPS, T_END
-    def make_opts(tol, ratio=STEP_TOL_RATIO):
-        return api.mgrit_opts(levels=3, m=(16, 16), space_level=(ids[2], ids[0], ids[0]), relax=1, tol=tol,
-                              max_iter=60, step_tol_ratio=ratio)
+    key = args.workload
+    w, meshes, model, ctx, ids, stream = workload_setup(key, local)
+    fine = ids[w.fine_level]
+    n = ctx.mg_num_dofs(fine)
+    N, T = w.N, w.T
+    space = tuple(ids[w.fine_level if args.no_sc else s_] for s_ in w.space_levels)
+
+    def make_opts(tol, precision=w.precision, ratio=STEP_TOL_RATIO):
+        return api.mgrit_opts(levels=w.levels, m=w.m, space_level=space, relax=w.relax, tol=tol, max_iter=60,
+                              step_tol_ratio=ratio, solver=api.solver_opts(precision=precision),
+                              nested=w.nonlinear)
+
     a0 = torch.zeros(n, dtype=torch.float64, device=dev)
     out = torch.empty((N + 1, n), dtype=torch.float64, device=dev)
 
     # launch shapes: the library's autotuner, once per (mesh, columns) the solve and
-    # the sequential baseline use (level-0 batches of 256 columns and single steps
-    # on the 18,240-DOF mesh; 256-, 16- and 1-column batches on the 1,104-DOF mesh)
+    # the sequential baseline use (linear meshes only)
     tuned = {}
-    if not args.no_autotune:
-        for lvl, kk in ((2, N // 16), (2, 1), (0, N // 16), (0, N // 256), (0, 1)):
-            so, ms = ctx.mg_autotune(ids[lvl], N // (1 if lvl == 2 else 16), T, kk)
+    if not args.no_autotune and not w.nonlinear:
+        shapes, stride = [(w.fine_level, 1)], 1
+        for l, m_l in enumerate(w.m):
+            shapes.append((w.space_levels[l], N // stride // m_l))
+            stride *= m_l
+        shapes.append((w.space_levels[-1], 1))
+        for lvl, kk in dict.fromkeys(shapes):
+            so, ms = ctx.mg_autotune(ids[lvl], N, T, kk)
             tuned["%d_DOFs_x%d" % (ctx.mg_num_dofs(ids[lvl]), kk)] = {
                 "path": "graph" if so.path == 2 else "cluster", "tile": so.tile, "cluster": so.cluster,
                 "rows_per_block": so.rows_per_block, "coarse_rows_per_block": so.coarse_rows_per_block,
@@ -372,25 +450,49 @@ def run_ours(args, rank, world, local):
 
             td.barrier()
 
-    # reference: sequential stepping with every step solved to 1e-13
-    ref = torch.empty((N + 1, n), dtype=torch.float64, device=dev)
-    ctx.mg_sequential(ids[2], N, T, a0, ref)
+    # error reference: sequential stepping with every step solved to 1e-13 (linear);
+    # nonlinear: sequential Newton stepping on the leading NONLINEAR_SEQ_PREFIX steps
+    # (also the timed sequential sample)
+    if w.nonlinear:
+        Kp = NONLINEAR_SEQ_PREFIX
+        ref = torch.empty((Kp + 1, n), dtype=torch.float64, device=dev)
+        ctx.mg_sequential(fine, 8, T * 8 / N, a0, ref[:9])  # warm-up: plans
+        torch.cuda.synchronize()
+        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0_.record(stream)
+        _, seq_st = ctx.mg_sequential(fine, Kp, T * Kp / N, a0, ref)
+        e1_.record(stream)
+        torch.cuda.synchronize()
+        seq_prefix_s = e0_.elapsed_time(e1_) / 1e3
+        ref_note = "GPU sequential Newton stepping (Newton to 1e-8) on the first %d steps" % Kp
+    else:
+        ref = torch.empty((N + 1, n), dtype=torch.float64, device=dev)
+        ref_note = "GPU sequential stepping, every step solved to 1e-13"
+        ctx.mg_sequential(fine, N, T, a0, ref)
 
     def max_rel_err(b):
-        diff = torch.linalg.vector_norm(b[1:] - ref[1:], dim=1) / torch.linalg.vector_norm(ref[1:], dim=1)
+        hi = ref.shape[0]  # the whole trajectory, or the reference's leading steps
+        diff = torch.linalg.vector_norm(b[1:hi] - ref[1:hi], dim=1) / torch.linalg.vector_norm(ref[1:hi], dim=1)
         return float(diff.max())
 
     # warm-up doubles as calibration: the loosest relative residual tolerance of the
     # ladder whose solution is within ERR_MARGIN * ERR_TARGET of the reference
-    tol = TOL_LADDER[-1]
-    calib = []
-    for t_try in TOL_LADDER:
-        ctx.mg_solve(N, T, a0, out, make_opts(t_try), allow=(-7,))
-        e = max_rel_err(out)
-        calib.append((t_try, e))
-        if e <= ERR_MARGIN * ERR_TARGET:
-            tol = t_try
-            break
+    def calibrate(precision):
+        tol = TOL_LADDER[-1]
+        calib = []
+        for t_try in TOL_LADDER:
+            ctx.mg_solve(N, T, a0, out, make_opts(t_try, precision), allow=(-7, -10))
+            e = max_rel_err(out)
+            calib.append((t_try, e))
+            if e <= ERR_MARGIN * ERR_TARGET:
+                tol = t_try
+                break
+        return tol, calib
+
+    if w.nonlinear:
+        tol, calib = NONLINEAR_TOL, []
+    else:
+        tol, calib = calibrate(w.precision)
     opts = make_opts(tol)
     for _ in range(args.warmup):
         ctx.mg_solve(N, T, a0, out, opts)
@@ -414,44 +516,75 @@ def run_ours(args, rank, world, local):
     t_step = max_over_ranks(t_step, world, dev)
     value = world * N / t_step
 
+    # the other arithmetic form, calibrated and timed the same way (FP32+refinement
+    # workloads: the FP64 form beside it)
+    alt = None
+    if w.precision == 1:
+        tol_a, calib_a = calibrate(0)
+        opts_a = make_opts(tol_a, 0)
+        ctx.mg_solve(N, T, a0, out, opts_a)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, st_a = ctx.mg_solve(N, T, a0, out, opts_a)
+        e1.record(stream)
+        barrier()
+        ta = e0.elapsed_time(e1) / 1e3 / args.steps
+        alt = {"form": "fp64", "wall_s": ta, "time_steps_per_s": N / ta, "mgrit_tol_rel": tol_a,
+               "iters": st_a["iters"], "pcg_iters": st_a["cg_iters"], "tolerance_calibration": calib_a,
+               "max_rel_err_vs_reference": max_rel_err(out), "step_solves_per_s": st_a["step_solves"] / ta}
+
     # end to end through the host-buffer entry point (pinned host memory)
     a0_h = torch.zeros(n, dtype=torch.float64).pin_memory()
     out_h = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
     a0_np, out_np = a0_h.numpy(), out_h.numpy()
-    ctx.mg_solve_host(N, T, a0_np, out_np, opts)
+    if not w.nonlinear:  # warm (a nonlinear solve takes minutes; its plans exist already)
+        ctx.mg_solve_host(N, T, a0_np, out_np, opts)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.mg_solve_host(N, T, a0_np, out_np, opts)
     barrier()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+    e2e_err = max_rel_err(torch.as_tensor(out_np).to(dev))
+    del out_h
 
-    roof = roofline(ctx, ids, N, T, stream)
+    roof = roofline(ctx, ids, w, stream)
 
     # GPU sequential stepping, the baseline: its steps solved to the loosest tolerance
     # of a ladder that keeps the trajectory within ERR_MARGIN * ERR_TARGET of the
-    # reference (the calibration runs warm it up), then timed once
-    seq = torch.empty((N + 1, n), dtype=torch.float64, device=dev)
-    seq_tol = SEQ_TOL_LADDER[-1]
-    seq_calib = []
-    for c_try in SEQ_TOL_LADDER:
-        ctx.mg_sequential(ids[2], N, T, a0, seq, solver=api.solver_opts(cg_tol=c_try, **SEQ_SMOOTHING))
-        e = max_rel_err(seq)
-        seq_calib.append((c_try, e))
-        if e <= ERR_MARGIN * ERR_TARGET:
-            seq_tol = c_try
-            break
-    seq_so = api.solver_opts(cg_tol=seq_tol, **SEQ_SMOOTHING)
-    barrier()
-    e0.record(stream)
-    _, seq_st = ctx.mg_sequential(ids[2], N, T, a0, seq, solver=seq_so)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    seq_s = e0.elapsed_time(e1) / 1e3
+    # reference (the calibration runs warm it up), then timed once; nonlinear: the
+    # default Newton tolerance, timed on the leading steps and extrapolated to N
+    if w.nonlinear:
+        Kp = NONLINEAR_SEQ_PREFIX
+        seq_s = seq_prefix_s * N / Kp
+        seq_tol, seq_calib = None, []
+        seq_err = 0.0  # it is the reference
+        seq_note = "timed on the first %d steps, extrapolated to N = %d" % (Kp, N)
+    else:
+        seq = torch.empty((N + 1, n), dtype=torch.float64, device=dev)
+        seq_tol = SEQ_TOL_LADDER[-1]
+        seq_calib = []
+        for c_try in SEQ_TOL_LADDER:
+            ctx.mg_sequential(fine, N, T, a0, seq, solver=api.solver_opts(cg_tol=c_try, **SEQ_SMOOTHING))
+            e = max_rel_err(seq)
+            seq_calib.append((c_try, e))
+            if e <= ERR_MARGIN * ERR_TARGET:
+                seq_tol = c_try
+                break
+        seq_so = api.solver_opts(cg_tol=seq_tol, **SEQ_SMOOTHING)
+        barrier()
+        e0.record(stream)
+        _, seq_st = ctx.mg_sequential(fine, N, T, a0, seq, solver=seq_so)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_s = e0.elapsed_time(e1) / 1e3
+        seq_err = max_rel_err(seq)
+        seq_note = "full run"
+        del seq
 
     max_err = max_rel_err(mgrit_out)
-    seq_err = max_rel_err(seq)
-    e2e_err = max_rel_err(torch.as_tensor(out_np).to(dev))
+    oracle = oracle_check(args, key, w, meshes, model, mgrit_out, ref) if rank == 0 else None
 
     st = stats[-1]
     dso = api.solver_opts()
@@ -466,32 +599,37 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if w.precision == 0 else "f32+f64",
         "data": "synthetic",
-        "config": dict(workload_config(n, ctx.mg_num_dofs(ids[0]), world), mgrit_tol_rel=tol,
+        "config": dict(workload_config(n, ctx.mg_num_dofs(ids[0]), world, key), mgrit_tol_rel=tol,
                        precond="multigrid V(%d,%d), Chebyshev smoothing on [lam/%g, lam], FP32, dense base inverse"
                                % (dso.smooth, dso.smooth, dso.cheb_ratio)),
-        "mgrit": {"wall_s": t_step, "iters": st["iters"], "res_hist": st["res_hist"],
-                  "step_tol_ratio": STEP_TOL_RATIO, "tolerance_calibration": calib,
-                  "max_rel_err_vs_reference": max_err, "step_solves": st["step_solves"],
-                  "batched_steps": st["batched_steps"], "pcg_iters": st["cg_iters"],
-                  "step_solves_per_s": st["step_solves"] / t_step},
+        "mgrit": {"form": "fp64" if w.precision == 0 else "fp32+fp64-refinement", "wall_s": t_step,
+                  "iters": st["iters"], "res_hist": st["res_hist"], "step_tol_ratio": STEP_TOL_RATIO,
+                  "tolerance_calibration": calib, "max_rel_err_vs_reference": max_err,
+                  "step_solves": st["step_solves"], "batched_steps": st["batched_steps"], "pcg_iters": st["cg_iters"],
+                  "newton_iters": st["newton_iters"], "step_solves_per_s": st["step_solves"] / t_step},
         "gpu_sequential": {"wall_s": seq_s, "time_steps_per_s": N / seq_s, "pcg_iters": seq_st["cg_iters"],
-                           "step_cg_tol": seq_tol, "smoothing": SEQ_SMOOTHING, "tolerance_calibration": seq_calib,
-                           "max_rel_err_vs_reference": seq_err},
+                           "newton_iters": seq_st["newton_iters"], "step_cg_tol": seq_tol,
+                           "smoothing": SEQ_SMOOTHING, "tolerance_calibration": seq_calib,
+                           "max_rel_err_vs_reference": seq_err, "timing": seq_note},
         "speedup_vs_gpu_sequential": seq_s / t_step,
-        "error_reference": "GPU sequential stepping, every step solved to 1e-13",
+        "error_reference": ref_note,
+        "spatial_coarsening": not args.no_sc,
+        "oracle_check": oracle,
         "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 8,
                 "d2h_bytes_per_step": (N + 1) * n * 8, "max_rel_err_vs_reference": e2e_err},
         "roofline": roof,
         "clocks": clocks.summary(),
-        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "gpu_launches": int(sum(s_["launches"] for s_ in stats)),
         "autotune": tuned,
         "wall_check_s": wall,
     }
+    if alt is not None:
+        line["mgrit_fp64"] = alt
     if rank == 0:
         if world == 1:
-            line["cpu_baseline"] = cpu_baseline(args)
+            line["cpu_baseline"] = cpu_baseline(args, key)
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -500,35 +638,71 @@ def run_ours(args, rank, world, local):
         td.destroy_process_group()
 
 
-def roofline(ctx, ids, N, T, stream):
-    """Time the dominant launch (one batched FP64 step at 18,240 DOFs x 256 columns
-    from the seeded start states of step_inputs, multigrid preconditioner) with CUDA
-    events and relate its algorithmic bytes to the measured HBM copy bandwidth."""
+def oracle_check(args, key, w, meshes, model, got, ref):
+    """The CPU oracle's sequential stepping (banded Cholesky, FP64) on the leading
+    time points; the maximal relative error per time point of the timed MGRIT
+    solve and of the GPU reference against it."""
+    import numpy as np
+
+    K = BENCH_WORKLOADS[key][2] if args.oracle_points < 0 else args.oracle_points
+    K = min(K, w.N)
+    if K <= 0 or w.nonlinear:
+        return None
+    from oracle.problem import MachineProblem, rel_err_per_point
+
+    t0 = time.perf_counter()
+    P = MachineProblem(meshes, model, w.N, w.T, (w.fine_level,), ())
+    phi = P.levels[0].phi
+    u = [np.zeros(P.n)]
+    for i in range(1, K + 1):
+        u.append(phi(u[-1], i))
+    u = np.array(u)
+    g = got[:K + 1].cpu().numpy()
+    r = ref[:K + 1].cpu().numpy()
+    return {"points": K, "max_rel_err_mgrit": float(rel_err_per_point(g, u).max()),
+            "max_rel_err_reference": float(rel_err_per_point(r, u).max()), "oracle_s": time.perf_counter() - t0}
+
+
+def roofline(ctx, ids, w, stream):
+    """Time the dominant launch (one batched step of the level-0 batch width on the
+    fine mesh from the seeded start states of step_inputs, in the workload's
+    arithmetic form, the library's own graph-path shape as in its DRAM capture)
+    with CUDA events.  achieved: the survey's unit (76 B per unknown x column x PCG
+    iteration in the FP64 form, 38 B with FP32 Krylov vectors) over the launch
+    time; achieved_all_passes: every vector pass of the multigrid-preconditioned
+    iteration, as bench's byte model counts it."""
     import torch
 
     from paper_1912_03106_gb300 import api
 
-    n = ctx.mg_num_dofs(ids[2])
-    k = 256
-    x_in, x_out = step_inputs(ctx, ids, k)
-    so = api.solver_opts(path=2)  # the library's own graph-path shape, as in the DRAM capture
-    ctx.mg_step(ids[2], N, T, x_in, x_out, i0=1, istride=1, solver=so)
+    if w.nonlinear:
+        return {"bound": "hbm", "kernel": "batched Newton step", "achieved": None, "peak": None, "unit": "GB/s",
+                "frac": None, "traffic": None,
+                "note": "no byte model for the Newton step; the linear workloads carry the PCG roofline"}
+    lvl = w.fine_level
+    n = ctx.mg_num_dofs(ids[lvl])
+    k = w.N // w.m[0]
+    x_in, x_out = step_inputs(ctx, ids, k, lvl)
+    so = api.solver_opts(path=2 if k >= 16 else 0, precision=w.precision)
+    ctx.mg_step(ids[lvl], w.N, w.T, x_in, x_out, i0=1, istride=1, solver=so)
     reps = 5
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     iters = 0
     for _ in range(reps):
-        _, st = ctx.mg_step(ids[2], N, T, x_in, x_out, i0=1, istride=1, solver=so)
+        _, st = ctx.mg_step(ids[lvl], w.N, w.T, x_in, x_out, i0=1, istride=1, solver=so)
         iters += st["cg_iters"]
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
     it_per_col = iters / reps / k
-    ns = [n, ctx.mg_num_dofs(ids[1]), ctx.mg_num_dofs(ids[0])]
-    per_col = step_bytes_per_column_iteration(ns, nu=so.smooth)
+    ns = [ctx.mg_num_dofs(ids[d]) for d in range(lvl, -1, -1)]
+    kb = 8 if w.precision == 0 else 4
+    per_col = step_bytes_per_column_iteration(ns, nu=so.smooth, krylov_bytes=kb)
     mat = matrix_bytes_per_iteration(ns, nu=so.smooth)
-    bytes_launch = it_per_col * (k * per_col + mat) + k * n * 8 * 9
+    bytes_all = it_per_col * (k * per_col + mat) + k * n * 8 * 9
+    bytes_survey = survey_bytes_per_unit(w.precision) * n * k * it_per_col
     peak = None
     src = "fallback"
     try:
@@ -536,55 +710,81 @@ def roofline(ctx, ids, N, T, stream):
         src = "measured"
     except (OSError, KeyError, ValueError):
         peak = 6800.0
-    achieved = bytes_launch / t / 1e9
+    achieved = bytes_survey / t / 1e9
+    achieved_all = bytes_all / t / 1e9
+    resident = n * k * 8 < 129e6
     return {"bound": "hbm",
-            "kernel": "batched step, 18,240 DOFs x 256 columns, FP64 form (one graph of per-phase kernels)",
+            "kernel": "batched step, %d DOFs x %d columns, %s form" % (
+                n, k, "FP64" if w.precision == 0 else "FP32+refinement") + (
+                " (one graph of per-phase kernels)" if k >= 16 else " (cluster-persistent kernel)"),
             "achieved": achieved, "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic(), "launch_ms": t * 1e3, "pcg_iters_per_column": it_per_col,
-            "algorithmic_bytes_per_launch": bytes_launch}
+            "achieved_all_passes": achieved_all, "frac_all_passes": achieved_all / peak,
+            "traffic": measured_traffic() if (lvl == 2 and k == 256 and w.precision == 0) else None,
+            "launch_ms": t * 1e3, "pcg_iters_per_column": it_per_col,
+            "algorithmic_bytes_per_launch": bytes_survey, "all_pass_bytes_per_launch": bytes_all,
+            "l2_resident": resident}
 
 
-def cpu_baseline(args):
-    """The oracle's sequential stepping (banded Cholesky, FP64) on a bounded sample."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+ORACLE_THREADS = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def cpu_baseline(args, key="cfg1"):
+    """The oracle's sequential stepping (banded Cholesky, FP64; Newton with banded
+    Cholesky for the Brauer law) on a bounded sample of the workload, in a
+    subprocess whose BLAS runs on one thread."""
+    from synth.workloads import workload
+
+    w = workload(BENCH_WORKLOADS[key][0])
+    sample = min(w.N, 4 if w.nonlinear else args.cpu_sample)
+    env = dict(os.environ, **ORACLE_THREADS)
     code = (
         "import sys, time, json; sys.path.insert(0, %r)\n"
         "import numpy as np, synth\n"
         "from synth.model import PwmSpec, machine_model\n"
+        "from synth.workloads import workload\n"
         "from oracle.problem import MachineProblem\n"
-        "from oracle import stepper\n"
-        "ms = synth.mesh_hierarchy(3)\n"
-        "P = MachineProblem(ms, machine_model(pwm=PwmSpec(J0=1e6, f_carrier=%r)), %d, %r, (2,), ())\n"
+        "w = workload(%r)\n"
+        "ms = synth.mesh_hierarchy(w.fine_level + 1)\n"
+        "model = machine_model(nonlinear=w.nonlinear, pwm=PwmSpec(J0=w.J0, f_carrier=w.f_carrier))\n"
+        "P = MachineProblem(ms, model, w.N, w.T, (w.fine_level,), (), nonlinear=w.nonlinear)\n"
         "phi = P.levels[0].phi\n"
-        "u = np.zeros(P.n); t = time.perf_counter()\n"
+        "u = np.zeros(P.n); phi(u, 1); t = time.perf_counter()\n"
         "for i in range(1, %d + 1): u = phi(u, i)\n"
         "dt = time.perf_counter() - t\n"
-        "print(json.dumps({'steps': %d, 'seconds': dt}))\n"
-    ) % (ROOT, F_CARRIER, N_STEPS, T_END, args.cpu_sample, args.cpu_sample)
+        "print(json.dumps({'steps': %d, 'seconds': dt, 'n': int(P.n)}))\n"
+    ) % (ROOT, w.name, sample, sample)
     try:
-        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
         res = json.loads(r.stdout.strip().splitlines()[-1])
+        how = ("damped Newton, each correction by banded Cholesky" if w.nonlinear else
+               "banded Cholesky factored once (factorisation not timed)")
         return {"value": res["steps"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"first {res['steps']} of {N_STEPS} backward-Euler steps of the 18,240-DOF model, "
-                          "sequential, banded Cholesky factored once (factorisation not timed)"}
+                "sample": f"first {res['steps']} of {w.N} backward-Euler steps of the {res['n']:,}-DOF model, "
+                          f"sequential, {how}; BLAS on one thread"}
     except Exception as e:  # pragma: no cover
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
 
 # ---------------------------------------------------------------- reference arm (the oracle)
 def run_reference(args, rank, world):
+    """The oracle's sequential stepping timed on the host: the reference arm.  Its
+    BLAS is pinned to one thread (set in main() before numpy loads)."""
     if rank != 0:
         return
     import numpy as np
 
     import synth
     from synth.model import PwmSpec, machine_model
+    from synth.workloads import workload
     from oracle.problem import MachineProblem
 
-    ms = synth.mesh_hierarchy(3)
-    P = MachineProblem(ms, machine_model(pwm=PwmSpec(J0=1e6, f_carrier=F_CARRIER)), N_STEPS, T_END, (2,), ())
+    key = getattr(args, "workload", "cfg1")
+    w = workload(BENCH_WORKLOADS[key][0])
+    ms = synth.mesh_hierarchy(w.fine_level + 1)
+    model = machine_model(nonlinear=w.nonlinear, pwm=PwmSpec(J0=w.J0, f_carrier=w.f_carrier))
+    P = MachineProblem(ms, model, w.N, w.T, (w.fine_level,), (), nonlinear=w.nonlinear)
     phi = P.levels[0].phi
-    sample = 32
+    sample = min(w.N, 2 if w.nonlinear else 32)
 
     def step():
         u = np.zeros(P.n)
@@ -598,14 +798,17 @@ def run_reference(args, rank, world):
     times = [step() for _ in range(args.steps)]
     t_step = sum(times) / len(times)
     value = sample / t_step
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = os.environ.get("OPENBLAS_NUM_THREADS", "")
+    cores = int(threads) if threads.isdigit() else (
+        len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": workload_config(P.n, len(ms[0].interior_nodes()), world),
+        "config": workload_config(P.n, len(ms[0].interior_nodes()), world, key),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} sequential backward-Euler steps of the 18,240-DOF model per step"},
+                         "sample": f"{sample} sequential backward-Euler steps of the {P.n:,}-DOF model per step, "
+                                   f"BLAS on {cores} thread(s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -621,6 +824,7 @@ def main():
         return
     rank, world, local = dist_info()
     if args.impl == "reference":
+        os.environ.update(ORACLE_THREADS)  # before numpy is first imported
         run_reference(args, rank, world)
         return
     run_ours(args, rank, world, local)

@@ -83,6 +83,21 @@ mg_status mg_add_mesh(mg_ctx* ctx, int* level_out, int64_t n_nodes, const double
  * the two levels; transfers across several refinements are composed. */
 mg_status mg_add_refinement(mg_ctx* ctx, int fine_level, int coarse_level, const int32_t* parent);
 
+/* Spatial transfer between two added meshes given as a matrix (Sec. 3.4: FE nodal
+ * interpolation P_s from the coarse to the fine mesh, Algorithm 1's interpolation;
+ * Sec. 2.2 spatial coarsening).  P is node-indexed CSR over ALL nodes (Dirichlet
+ * ones included): rowptr[n_nodes(fine) + 1] (int64, rowptr[0] = 0, rowptr[end] =
+ * nnz), col[nnz] coarse node ids, val[nnz] weights; host arrays, copied.  The node
+ * sets must be nested: every coarse node has a fine node whose row of P is that
+ * coarse node's unit vector (one entry, weight exactly 1); MGRIT restricts states by
+ * injection at those nodes and residuals by P^T as restrict_mode says.  Meshes need
+ * not come from red refinement (e.g. a barycentric split).  For MGRIT levels on the
+ * pair (fine, coarse) this matrix replaces a transfer composed from refinements;
+ * the step solver's multigrid preconditioner still uses refinements only.
+ * MG_EINVAL for bad levels, indices, non-finite weights or non-nested node sets. */
+mg_status mg_add_transfer(mg_ctx* ctx, int fine_level, int coarse_level, int64_t nnz, const int64_t* rowptr,
+                          const int32_t* col, const double* val);
+
 /* Material of a region tag (Sec. 3.1; Sec. 5 for the Brauer law):
  * law 0: nu constant; law 1: nu(|B|^2) = k1 exp(k2 |B|^2) + k3 (nu unused). */
 mg_status mg_set_material(mg_ctx* ctx, int32_t region, double sigma, double nu, int law,
@@ -155,10 +170,13 @@ typedef struct {
      * one FP32 geometric-multigrid V-cycle over the nested meshes (coarsest mesh
      * solved by a dense inverse) or by Jacobi */
     double cg_tol;      /* FP64 mode: stop at ||b - L x|| <= cg_tol ||b|| per column      */
-    double refine_tol;  /* FP32+refinement: outer FP64 stop ||b - L x|| <= refine_tol ||b|| */
-    double inner_tol;   /* FP32+refinement: inner FP32 PCG relative reduction per sweep    */
-    int max_cg;         /* iteration limit of one (inner) PCG                              */
-    int max_refine;     /* FP32+refinement: limit of outer sweeps                          */
+    double refine_tol;  /* FP32+refinement: FP64 stop ||b - L x|| <= refine_tol ||b||        */
+    double inner_tol;   /* FP32+refinement: the FP32 PCG runs on across FP64 residual updates
+                           (reliable updates): a column's FP64 residual b - L x is recomputed
+                           once its FP32 residual has fallen by inner_tol since the last one,
+                           or after 10 FP32 iterations without one                         */
+    int max_cg;         /* iteration limit of one PCG (FP32+refinement: of its FP32 iterations) */
+    int max_refine;     /* FP32+refinement: limit of FP64 residual updates                 */
     int precision;      /* mg_precision                                                    */
     int cluster;        /* CTAs per cluster (1..16; above 8 needs non-portable clusters), 0 = library
                            choice (16 for a single column tile when the device allows it, else 8) */
@@ -188,7 +206,7 @@ typedef struct {
 } mg_solver_opts;
 
 /* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,
- * inner_tol 1e-5, max_cg 2000, max_refine 30, FP64, multigrid with 5 Chebyshev
+ * inner_tol 3e-2, max_cg 2000, max_refine 30, FP64, multigrid with 5 Chebyshev
  * sweeps on [lam/30, lam] before and after each coarse correction (omega 0.7 for
  * MG_SMOOTH_JACOBI); newton_tol 1e-8, max_newton 100,
  * max_halvings 40, newton_lin_tol 1e-6). */
@@ -312,7 +330,8 @@ typedef struct {
                               change (the first entry infinite)                            */
     double step_tol_ratio; /* > 0: inexact step solves (no counterpart in the paper): the steps of
                               an iteration are solved to max(solver tolerance, step_tol_ratio x
-                              the current relative residual), so early iterations, whose iterate
+                              the current relative residual) -- cg_tol, refine_tol and, for
+                              Newton steps, newton_tol -- so early iterations, whose iterate
                               is still far from the solution, do not solve to full accuracy; the
                               converged result is unchanged. 0 (default): fixed tolerance    */
 } mg_opts;

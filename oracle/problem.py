@@ -15,7 +15,10 @@ from . import fem, mgrit, pwm, stepper, transfer
 
 class MachineProblem:
     def __init__(self, meshes, model, N: int, T: float, space_levels, m, nonlinear: bool = False,
-                 residual_mode: int = 2, newton_tol: float = 1e-8, t_ramp: float = 0.0):
+                 residual_mode: int = 2, newton_tol: float = 1e-8, t_ramp: float = 0.0, transfers=None):
+        """transfers: {(fine mesh index, coarse mesh index): node-space P_s} for pairs
+        whose transfer is given as a matrix rather than by red refinements."""
+        self.transfers = dict(transfers or {})
         self.meshes = meshes
         self.model = model
         self.N = N
@@ -53,7 +56,8 @@ class MachineProblem:
             if not last:
                 sc = self.space_levels[l + 1]
                 between = meshes[sc:s + 1]
-                tr = transfer.SpaceTransfer(self.fe[s], self.fe[sc], between, residual_mode)
+                tr = transfer.SpaceTransfer(self.fe[s], self.fe[sc], between, residual_mode,
+                                            node_P=self.transfers.get((s, sc)))
                 if N // stride % ml:
                     raise ValueError("N must be divisible by the product of the coarsening factors")
             levels.append(mgrit.Level(phi=phi, N=Nl, m=ml, transfer=tr))

@@ -56,16 +56,40 @@ def injection_index(fe_fine, fe_coarse, meshes_between) -> np.ndarray:
     return idx
 
 
-class SpaceTransfer:
-    """R_s / P_s between two MGRIT levels' space meshes (identity if equal)."""
+def injection_from_matrix(node_P: sp.csr_matrix, fe_fine, fe_coarse) -> np.ndarray:
+    """For each coarse interior DOF, the fine interior DOF at the same node, read
+    from a node-space P_s of nested node sets: the fine node whose row of P_s is
+    the coarse node's unit vector (nodal interpolation keeps coinciding values)."""
+    P = node_P.tocsr()
+    at = np.full(P.shape[1], -1, dtype=np.int64)
+    for i in range(P.shape[0]):
+        lo, hi = P.indptr[i], P.indptr[i + 1]
+        if hi - lo == 1 and P.data[lo] == 1.0:
+            at[P.indices[lo]] = i
+    fine_node = at[fe_coarse.dof]
+    assert np.all(fine_node >= 0), "coarse node that is not a fine node"
+    idx = fe_fine.node2dof[fine_node]
+    assert np.all(idx >= 0)
+    return idx
 
-    def __init__(self, fe_fine, fe_coarse, meshes_between, residual_mode: int = 2):
+
+class SpaceTransfer:
+    """R_s / P_s between two MGRIT levels' space meshes (identity if equal).
+
+    node_P: P_s given as a node-space matrix (fine nodes x coarse nodes) instead of
+    the product of the red refinements in meshes_between."""
+
+    def __init__(self, fe_fine, fe_coarse, meshes_between, residual_mode: int = 2, node_P=None):
         self.identity = fe_fine is fe_coarse
         self.mode = residual_mode
         if self.identity:
             return
-        self.P = prolongation(fe_fine, fe_coarse, meshes_between)
-        self.inj = injection_index(fe_fine, fe_coarse, meshes_between)
+        if node_P is None:
+            self.P = prolongation(fe_fine, fe_coarse, meshes_between)
+            self.inj = injection_index(fe_fine, fe_coarse, meshes_between)
+        else:
+            self.P = sp.csr_matrix(node_P)[fe_fine.dof][:, fe_coarse.dof].tocsr()
+            self.inj = injection_from_matrix(node_P, fe_fine, fe_coarse)
         self.PT = self.P.T.tocsr()
         self.D = np.asarray(self.PT @ np.ones(self.P.shape[0])).ravel()
 

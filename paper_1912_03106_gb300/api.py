@@ -134,6 +134,15 @@ class Context:
         parent = np.ascontiguousarray(parent, dtype=np.int32)
         self._check(self.lib.mg_add_refinement(self.h, fine, coarse, _ptr(parent)))
 
+    def mg_add_transfer(self, fine: int, coarse: int, rowptr, col, val):
+        """P_s (fine <- coarse) as node-indexed CSR arrays (e.g. a scipy csr_matrix's
+        indptr, indices, data)."""
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        self._check(self.lib.mg_add_transfer(self.h, fine, coarse, int(rowptr[-1]), _ptr(rowptr), _ptr(col),
+                                             _ptr(val)))
+
     def mg_set_material(self, region, sigma, nu, law=0, k1=0.0, k2=0.0, k3=0.0):
         self._check(self.lib.mg_set_material(self.h, region, sigma, nu, law, k1, k2, k3))
 

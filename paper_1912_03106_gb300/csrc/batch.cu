@@ -79,7 +79,7 @@ struct CallArgs {
     int64_t t0, tstride;
     int k;
     double tol2;        // FP64 form: cg_tol^2; FP32+refine: refine_tol^2
-    double inner_tol2;  // FP32+refine inner reduction^2
+    double inner_tol2;  // FP32+refine: reduction^2 of the FP32 residual that triggers an FP64 update
     // rounding floor of the FP64 residual b - L x: a column whose computed residual
     // satisfies ||r||^2 <= fl_acc2 * S^2, S = || |b| + |L| |x| ||, is a solution to
     // working precision (its initial guess is kept, refinement stops); the PCG
@@ -103,12 +103,18 @@ struct Depth {
     const int32_t* rt_col;
     const float* rt_w;
     float *x, *sa, *sb, *y, *r;
+    // per column tile: 0 once all of its columns have stopped iterating; the PCG and
+    // multigrid kernels then skip the tile (its vectors and partials stay as they are)
+    const int* tact;
 };
 
 struct Cols {
     double *bb, *gam, *beta, *alpha, *ref, *prev, *ss;  // ss: S^2 of the rounding floor
     int *act, *outer, *iters;
     int* bad;  // a non-finite residual or right-hand side was seen (reported as MG_ENONFINITE)
+    int *upd, *nup, *stall;  // FP32+refine: FP64 update due, updates done, updates without progress
+    int* lastu;              // FP32+refine: the column's iteration count at its last FP64 update
+    int* tact;               // per tile: any column still iterating (see Depth::tact)
     int* ctr;  // [0] iterations of the current PCG, [1] refinement sweep
 };
 
@@ -116,6 +122,9 @@ __device__ __forceinline__ void tile_rb(int nrb, int& t, int& rb) {
     t = blockIdx.x / nrb;
     rb = blockIdx.x - t * nrb;
 }
+
+// false once every column of tile t has stopped iterating (block-uniform)
+__device__ __forceinline__ bool tile_on(const int* tact, int t) { return !tact || __ldg(tact + t) != 0; }
 
 // Per-block, per-column sum of the thread's V column partials into part[blockIdx.x * G + c].
 template <int V>
@@ -153,12 +162,14 @@ template <class T>
 __device__ __forceinline__ T* tv(T* base, int n, int t) { return base + (size_t)t * n * G; }
 
 // ---------------------------------------------------------------- set-up and final phases
-// b = (1/dt) M x_prev + J0 sum_s b_s F_s, x0 = guess - g; FP64 form: r = b - L x0.
+// b = (1/dt) M x_prev + J0 sum_s b_s F_s, x0 = guess - g; FP64 form: r = b - L x0;
+// FP32+refinement: b kept, the FP32 correction and Krylov vectors d, p, q zeroed.
 template <int MODE>
 __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restrict__ ca, double inv_dt,
                                                const double* __restrict__ F, double J0, double* x64, double* r64,
                                                double* p64, double* q64, double* b64, float* z, double* part_bb,
-                                               double* part_rr, double* part_ss, float* r32s) {
+                                               double* part_rr, double* part_ss, float* r32s, float* d32, float* p32,
+                                               float* q32) {
     phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
@@ -175,7 +186,8 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
     double bb[1] = {0.0}, rr[1] = {0.0}, ss[1] = {0.0};
     const int i1 = min(D.n, (rb + 1) * D.rbs);
     for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
-        double bi = 0.0, lx = 0.0, xi = 0.0, alx = 0.0;
+        double bi = 0.0, lx = 0.0, xi = 0.0;
+        float alx = 0.0f;  // sum |L_ij| |x_j| of the rounding floor (an estimate: FP32)
         if (valid) {
             double mb = 0.0;
             for (int w = 0; w < D.W; ++w) {
@@ -184,9 +196,8 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
                 if (guess) {
                     double xj = guess[j * ca->ld_guess + gc];
                     if (g) xj -= g[j * ca->ld_g + gc];
-                    const double a = __ldg(D.L64 + w * D.n + i);
-                    lx += a * xj;
-                    alx += fabs(a) * fabs(xj);
+                    lx += __ldg(D.L64 + w * D.n + i) * xj;
+                    alx += fabsf(__ldg(D.L32 + w * D.n + i)) * abs_to_float(xj);
                 }
             }
             bi = mb * inv_dt + J0 * (sg[0] * F[i] + sg[1] * F[D.n + i] + sg[2] * F[2 * D.n + i]);
@@ -205,10 +216,13 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
             p64[o] = 0.0;
             q64[o] = 0.0;
             rr[0] += ri * ri;
-            const double si = fabs(bi) + alx;
-            ss[0] += si * si;
+            const float si = abs_to_float(bi) + alx;
+            ss[0] += (double)(si * si);
         } else {
             b64[o] = bi;
+            d32[o] = 0.0f;
+            p32[o] = 0.0f;
+            q32[o] = 0.0f;
         }
         bb[0] += bi * bi;
     }
@@ -221,8 +235,9 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
     }
 }
 
-// x_out = x + g
-__global__ void __launch_bounds__(NTB) kb_final(Depth D, const CallArgs* __restrict__ ca, const double* x64) {
+// x_out = x (+ d: the FP32 correction not yet folded into x) + g
+__global__ void __launch_bounds__(NTB) kb_final(Depth D, const CallArgs* __restrict__ ca, const double* x64,
+                                                const float* d32) {
     phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
@@ -231,6 +246,7 @@ __global__ void __launch_bounds__(NTB) kb_final(Depth D, const CallArgs* __restr
     const int i1 = min(D.n, (rb + 1) * D.rbs);
     for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
         double xi = x64[((size_t)t * D.n + i) * G + lc];
+        if (d32) xi += (double)d32[((size_t)t * D.n + i) * G + lc];
         if (ca->g) xi += ca->g[(int64_t)i * ca->ld_g + gc];
         ca->xout[(int64_t)i * ca->ld_out + gc] = xi;
     }
@@ -262,6 +278,11 @@ __global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* pa
         any |= a;
     }
     any = __syncthreads_or(any);
+    for (int t = threadIdx.x; t < kpad / G; t += NSB) {
+        int on = 0;
+        for (int l = 0; l < G; ++l) on |= st.act[t * G + l];
+        st.tact[t] = on;
+    }
     if (threadIdx.x == 0) {
         st.ctr[0] = 0;
         st.ctr[2] = 0;
@@ -270,24 +291,27 @@ __global__ void __launch_bounds__(NSB) kb_scalar_init0(Cols st, const double* pa
     }
 }
 
-// FP32+refinement: ||b||^2, every column starts in the refinement loop.
+// FP32+refinement: ||b||^2; every valid column starts with an FP64 residual update.
 __global__ void __launch_bounds__(NSB) kb_scalar_init1(Cols st, const double* part_bb, int nrb, int kpad,
-                                                      const CallArgs* __restrict__ ca, cudaGraphConditionalHandle h,
-                                                      int use_cond) {
+                                                      const CallArgs* __restrict__ ca) {
     phase_begin();
     for (int c = threadIdx.x; c < kpad; c += NSB) {
         const double bb = col_total(part_bb, nrb, c);
         st.bb[c] = bb;
         st.outer[c] = c < ca->k;
+        st.upd[c] = c < ca->k;
+        st.nup[c] = 0;
+        st.stall[c] = 0;
+        st.lastu[c] = 0;
         st.iters[c] = 0;
         st.act[c] = 0;
+        st.gam[c] = 0.0;
         st.bad[c] = (c < ca->k) && !(bb - bb == 0.0);
     }
     if (threadIdx.x == 0) {
-        st.ctr[1] = 0;
+        st.ctr[0] = 0;
         st.ctr[2] = 0;
         st.ctr[3] = 0;
-        if (use_cond) cudaGraphSetConditional(h, 1u);
     }
 }
 
@@ -353,6 +377,7 @@ __global__ void __launch_bounds__(NTB) kb_scalar_conv(Cols st, const double* par
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
+        st.tact[blockIdx.x] = any;
         if (any) atomicAdd(&st.ctr[2], 1);
         __threadfence();
         const unsigned ticket = atomicAdd(reinterpret_cast<unsigned*>(&st.ctr[3]), 1u);
@@ -367,41 +392,99 @@ __global__ void __launch_bounds__(NTB) kb_scalar_conv(Cols st, const double* par
     }
 }
 
-// refinement decisions after r = b - L64 x; sets the inner and outer loop conditions
-__global__ void __launch_bounds__(NSB) kb_scalar_refine(Cols st, const double* part, const double* part_ss, int nrb,
-                                                       int kpad, const CallArgs* __restrict__ ca,
-                                                       cudaGraphConditionalHandle h_inner,
-                                                       cudaGraphConditionalHandle h_outer, int use_cond) {
+// FP32+refinement, after an FP32 iteration: a column whose FP32 residual has fallen
+// by inner_tol since its last FP64 residual, or below the tolerance, gets an FP64
+// update (the residual replacement of the reliable-update scheme); the last tile
+// block advances the iteration count.
+__global__ void __launch_bounds__(NTB) kb_scalar_conv_ru(Cols st, const double* part, int nrb,
+                                                        const CallArgs* __restrict__ ca) {
     phase_begin();
-    const int sweep = st.ctr[1];
-    int any = 0;
-    for (int c = threadIdx.x; c < kpad; c += NSB) {
-        const double rr = col_total(part, nrb, c);
-        if (st.outer[c] == 1) {
-            // tolerance met, or x solves the step to working precision (the initial
-            // guess within the acceptance margin, a refined iterate at the floor itself)
-            const double fl2 = sweep == 0 ? ca->fl_acc2 : ca->fl_stop2;
-            const bool met = rr <= ca->tol2 * st.bb[c] || rr <= fl2 * col_total(part_ss, nrb, c);
-            const bool stalled = sweep > 0 && rr > 0.25 * st.prev[c];
-            if (met || (stalled && rr <= 1e-16 * st.bb[c])) st.outer[c] = 0;
-            else if (stalled || sweep >= ca->max_refine || !(rr - rr == 0.0)) st.outer[c] = 2;
-            if (!(rr - rr == 0.0)) st.bad[c] = 1;
+    __shared__ double rr[G];
+    tile_totals(part, nrb, blockIdx.x, rr);
+    if (threadIdx.x < G) {
+        const int c = blockIdx.x * G + threadIdx.x;
+        const double v = rr[threadIdx.x];
+        int u = 0;
+        if (st.act[c]) {
+            st.iters[c] += 1;
+            if (!(v - v == 0.0)) {
+                st.bad[c] = 1;
+                st.act[c] = 0;
+                st.outer[c] = 2;
+            } else {
+                u = v <= ca->inner_tol2 * st.ref[c] || v <= ca->tol2 * st.bb[c] ||
+                    st.iters[c] - st.lastu[c] >= kMaxInner;
+                if (u) st.prev[c] = v;  // the FP32 residual the FP64 one is compared with
+            }
         }
-        const int a = st.outer[c] == 1;
-        st.act[c] = a;
-        st.ref[c] = rr;
-        st.prev[c] = rr;
-        st.gam[c] = 0.0;
-        any |= a;
+        st.upd[c] = u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(reinterpret_cast<unsigned*>(&st.ctr[3]), 1u);
+        if (ticket == gridDim.x - 1) {
+            __threadfence();
+            st.ctr[3] = 0;
+            st.ctr[0] = st.ctr[0] + 1;
+        }
+    }
+}
+
+// FP32+refinement: decisions after the FP64 residual of the updated columns.  A
+// column stops when ||r|| meets the tolerance or the rounding floor (the initial
+// guess within the acceptance margin), fails when the residual is not finite, the
+// updates exceed max_refine or three updates in a row took less than 10 % off ||r||
+// above the acceptance margin; otherwise the FP32 iteration continues from the new
+// residual.
+// The last tile block sets the loop condition: columns left and iterations left.
+__global__ void __launch_bounds__(NTB) kb_scalar_ru(Cols st, const double* part_rr, const double* part_ss, int nrb,
+                                                   const CallArgs* __restrict__ ca, cudaGraphConditionalHandle h,
+                                                   int use_cond) {
+    phase_begin();
+    __shared__ double rr[G], ss[G];
+    tile_totals(part_rr, nrb, blockIdx.x, rr);
+    tile_totals(part_ss, nrb, blockIdx.x, ss);
+    int any = 0;
+    if (threadIdx.x < G) {
+        const int c = blockIdx.x * G + threadIdx.x;
+        if (st.upd[c] && st.outer[c] == 1) {
+            const double v = rr[threadIdx.x], sv = ss[threadIdx.x];
+            const bool first = st.nup[c] == 0;
+            const double fl2 = first ? ca->fl_acc2 : ca->fl_stop2;
+            if (!(v - v == 0.0)) {
+                st.bad[c] = 1;
+                st.outer[c] = 2;
+            } else if (v <= ca->tol2 * st.bb[c] || v <= fl2 * sv) {
+                st.outer[c] = 0;
+            } else {
+                if (!first && v > 0.81 * st.ref[c]) st.stall[c] += 1;
+                else st.stall[c] = 0;
+                if (st.stall[c] >= 3) st.outer[c] = v <= ca->fl_acc2 * sv ? 0 : 2;
+                else if (st.nup[c] > ca->max_refine) st.outer[c] = 2;
+            }
+            // the FP32 recurrence had drifted from the true residual by more than 2x:
+            // its search direction no longer fits, restart it (beta = 0)
+            if (!first && v > 4.0 * st.prev[c]) st.gam[c] = 0.0;
+            st.nup[c] += 1;
+            st.ref[c] = v;
+            st.lastu[c] = st.iters[c];
+            st.act[c] = st.outer[c] == 1;
+        }
+        any = st.act[c];
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-        st.ctr[0] = 0;
-        st.ctr[1] = sweep + 1;
-        st.ctr[2] = 0;
-        st.ctr[3] = 0;
-        if (use_cond) cudaGraphSetConditional(h_inner, (any && ca->max_it > 0) ? 1u : 0u);
-        if (use_cond) cudaGraphSetConditional(h_outer, any ? 1u : 0u);
+        st.tact[blockIdx.x] = any;
+        if (any) atomicAdd(&st.ctr[2], 1);
+        __threadfence();
+        const unsigned ticket = atomicAdd(reinterpret_cast<unsigned*>(&st.ctr[3]), 1u);
+        if (ticket == gridDim.x - 1) {
+            __threadfence();
+            const int active = atomicExch(&st.ctr[2], 0);
+            st.ctr[3] = 0;
+            if (use_cond) cudaGraphSetConditional(h, (active && st.ctr[0] < ca->max_it) ? 1u : 0u);
+        }
     }
 }
 
@@ -419,13 +502,14 @@ __global__ void __launch_bounds__(NSB) kb_scalar_final(Cols st, int kpad, const 
 
 // Exact float -> double conversion with integer instructions: on GB300 the F2F
 // conversion issues on the FP64 pipe, whose rate is a small fraction of FP32's.
-// Normal numbers convert exactly; zero and denormals give (signed) zero; infinities
-// stay infinities and NaNs stay NaNs (exponent all ones maps to all ones, the
-// mantissa bits are kept), so a poisoned preconditioner output reaches the
-// convergence test instead of turning into a large finite number.
+// Normal numbers and zeros convert by moving bits; infinities stay infinities and
+// NaNs stay NaNs (exponent all ones maps to all ones, the mantissa bits are kept),
+// so a poisoned preconditioner output reaches the convergence test instead of
+// turning into a large finite number; the rare denormals take the hardware path.
 __device__ __forceinline__ double f2d_int(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u && (u & 0x7fffffu)) return (double)f;
     const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
     const unsigned long long mant = (unsigned long long)(u & 0x7fffffu) << 29;
     const unsigned long long ex = (unsigned long long)(e == 0xffu ? 0x7ffu : e + (1023u - 127u)) << 52;
@@ -500,6 +584,7 @@ constexpr int RPPF = NTB / TPRF;   // rows per pass
 #define ROWS_F(D, t, rb, i)                                   \
     int t, rb;                                                \
     tile_rb((D).nrb, t, rb);                                  \
+    if (!tile_on((D).tact, t)) return;                        \
     const int c0 = (threadIdx.x % TPRF) * VF;                 \
     const int _i1 = min((D).n, (rb + 1) * (D).rbs);           \
     for (int i = rb * (D).rbs + threadIdx.x / TPRF; i < _i1; i += RPPF)
@@ -509,69 +594,144 @@ __device__ __forceinline__ float sweep_weight(float w, const unsigned* lam) {
     return lam ? w / __uint_as_float(__ldg(lam)) : w;
 }
 
+// Launch shape of the gather-bound smoothing and residual-update kernels.  A thread
+// may take MG_SRB rows per batch, the loads of all of them (indices, values,
+// gathered neighbours) issued before any result is stored, so that their
+// latencies overlap; and MG_MINB_S (shared operators) or MG_MINB_PC (per-column
+// Newton Jacobians, four values per entry and lane) blocks of 256 threads must fit
+// an SM, which caps the registers of a thread.  Measured on GB300 (one batched FP64
+// step to 1e-13, 18,240 DOFs x 256 columns / 73,344 x 1,024): one row and 4 blocks
+// (64 registers) 5.40 / 76.3 ms; one row and 5 blocks (48 registers, spilling)
+// 6.60 / 92.6 ms; two rows and 3 blocks 6.36 / 84.5 ms; two rows and 4 blocks
+// 6.77 / 91.8 ms; four rows and 2 blocks 6.56 / 104.7 ms.  Spills, not the
+// latency of one row, were the cost.
+#ifndef MG_SRB
+#define MG_SRB 1
+#endif
+#ifndef MG_MINB_S
+#define MG_MINB_S 4
+#endif
+#ifndef MG_MINB_PC
+#define MG_MINB_PC 3
+#endif
+template <bool PC>
+__host__ __device__ constexpr int srb() { return PC ? 1 : MG_SRB; }
+template <bool PC>
+__host__ __device__ constexpr int minb_s() { return PC ? MG_MINB_PC : MG_MINB_S; }
+
 // x = w D^-1 r, s = r - w (L D^-1) r
 template <class RT, bool PC>
-__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth_first(Depth D, const RT* rin_base, float w0,
-                                                                  const unsigned* lam) {
+__global__ void __launch_bounds__(NTB, minb_s<PC>()) kb_smooth_first(Depth D, const RT* rin_base, float w0,
+                                                                     const unsigned* lam) {
+    constexpr int SRB = srb<PC>();
     phase_begin();
     const float w = sweep_weight(w0, lam);
-    ROWS_F(D, t, rb, i) {
-        const RT* rin = tv(rin_base, D.n, t);
-        RT rv[VF];
-        vld<RT, VF>(rin + i * G + c0, rv);
-        float acc[VF];
-        ell_vec_w<VF, float, float, RT, PC>(D.col, tile_vals<PC>(D.LD32, D, t), D.n, D.W, i, rin, c0, acc);
-        float di[VF];
-        dinv_of<PC>(D, t, i, c0, di);
-        float xo[VF], so[VF];
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    if (!tile_on(D.tact, t)) return;
+    const int c0 = (threadIdx.x % TPRF) * VF;
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    const RT* rin = tv(rin_base, D.n, t);
+    float* x = tv(D.x, D.n, t);
+    float* sa = tv(D.sa, D.n, t);
+    for (int i0 = rb * D.rbs + threadIdx.x / TPRF; i0 < i1; i0 += RPPF * SRB) {
+        RT rv[SRB][VF];
+        float acc[SRB][VF], di[SRB][VF];
 #pragma unroll
-        for (int e = 0; e < VF; ++e) {
-            xo[e] = w * di[e] * (float)rv[e];
-            so[e] = (float)rv[e] - w * acc[e];
+        for (int q = 0; q < SRB; ++q) {
+            const int i = i0 + q * RPPF;
+            if (i < i1) {
+                vld<RT, VF>(rin + i * G + c0, rv[q]);
+                ell_vec_w<VF, float, float, RT, PC>(D.col, tile_vals<PC>(D.LD32, D, t), D.n, D.W, i, rin, c0,
+                                                    acc[q]);
+                dinv_of<PC>(D, t, i, c0, di[q]);
+            }
         }
-        vst<float, VF>(tv(D.x, D.n, t) + i * G + c0, xo);
-        vst<float, VF>(tv(D.sa, D.n, t) + i * G + c0, so);
+#pragma unroll
+        for (int q = 0; q < SRB; ++q) {
+            const int i = i0 + q * RPPF;
+            if (i < i1) {
+                float xo[VF], so[VF];
+#pragma unroll
+                for (int e = 0; e < VF; ++e) {
+                    xo[e] = w * di[q][e] * (float)rv[q][e];
+                    so[e] = (float)rv[q][e] - w * acc[q][e];
+                }
+                vst<float, VF>(x + i * G + c0, xo);
+                vst<float, VF>(sa + i * G + c0, so);
+            }
+        }
     }
 }
 
 // x += w D^-1 s; s' = s - w (L D^-1) s if dst is given (not on a level's last sweep);
 // partial (r, x) if rtop is given (last sweep on the finest level)
 template <class RT, bool PC>
-__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_smooth(Depth D, const float* src_base, float* dst_base, const RT* rtop_base,
-                                                 float w0, const unsigned* lam, double* part) {
+__global__ void __launch_bounds__(NTB, minb_s<PC>()) kb_smooth(Depth D, const float* src_base, float* dst_base,
+                                                               const RT* rtop_base, float w0, const unsigned* lam,
+                                                               double* part) {
+    constexpr int SRB = srb<PC>();
     phase_begin();
     const float w = sweep_weight(w0, lam);
-    double rz[VF] = {0.0, 0.0, 0.0, 0.0};
-    {
-        ROWS_F(D, t, rb, i) {
-            const float* src = tv(src_base, D.n, t);
-            float* x = tv(D.x, D.n, t);
-            float sv[VF], xv[VF];
-            vld<float, VF>(src + i * G + c0, sv);
-            vld<float, VF>(x + i * G + c0, xv);
-            float di[VF];
-            dinv_of<PC>(D, t, i, c0, di);
-            float xo[VF];
+    // (r, x) of a thread's few rows: FP32 sums for shared operators (linear steps,
+    // where |r_i x_i| ~ r_i^2 / L_ii stays far inside the FP32 range); FP64 for
+    // Newton corrections, whose residuals near convergence are so small that FP32
+    // products of r and x would underflow
+    using RZ = typename std::conditional<PC, double, float>::type;
+    RZ rz[VF] = {};
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    if (!tile_on(D.tact, t)) return;
+    const int c0 = (threadIdx.x % TPRF) * VF;
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    const float* src = tv(src_base, D.n, t);
+    float* x = tv(D.x, D.n, t);
+    float* dst = dst_base ? tv(dst_base, D.n, t) : nullptr;
+    const RT* rtop = rtop_base ? tv(rtop_base, D.n, t) : nullptr;
+    for (int i0 = rb * D.rbs + threadIdx.x / TPRF; i0 < i1; i0 += RPPF * SRB) {
+        float sv[SRB][VF], xv[SRB][VF], di[SRB][VF], acc[SRB][VF];
+        RT rv[SRB][VF];
 #pragma unroll
-            for (int e = 0; e < VF; ++e) xo[e] = xv[e] + w * di[e] * sv[e];
-            vst<float, VF>(x + i * G + c0, xo);
-            if (rtop_base) {
-                RT rv[VF];
-                vld<RT, VF>(tv(rtop_base, D.n, t) + i * G + c0, rv);
-#pragma unroll
-                for (int e = 0; e < VF; ++e) rz[e] += (double)rv[e] * (double)xo[e];
+        for (int q = 0; q < SRB; ++q) {
+            const int i = i0 + q * RPPF;
+            if (i < i1) {
+                vld<float, VF>(src + i * G + c0, sv[q]);
+                vld<float, VF>(x + i * G + c0, xv[q]);
+                dinv_of<PC>(D, t, i, c0, di[q]);
+                if (rtop) vld<RT, VF>(rtop + i * G + c0, rv[q]);
+                // the next residual is needed unless this is the last sweep
+                if (dst)
+                    ell_vec_w<VF, float, float, float, PC>(D.col, tile_vals<PC>(D.LD32, D, t), D.n, D.W, i, src, c0,
+                                                           acc[q]);
             }
-            if (dst_base) {  // the next residual is needed unless this is the last sweep
-                float acc[VF];
-                ell_vec_w<VF, float, float, float, PC>(D.col, tile_vals<PC>(D.LD32, D, t), D.n, D.W, i, src, c0, acc);
-                float so[VF];
+        }
 #pragma unroll
-                for (int e = 0; e < VF; ++e) so[e] = sv[e] - w * acc[e];
-                vst<float, VF>(tv(dst_base, D.n, t) + i * G + c0, so);
+        for (int q = 0; q < SRB; ++q) {
+            const int i = i0 + q * RPPF;
+            if (i < i1) {
+                float xo[VF];
+#pragma unroll
+                for (int e = 0; e < VF; ++e) xo[e] = xv[q][e] + w * di[q][e] * sv[q][e];
+                vst<float, VF>(x + i * G + c0, xo);
+                if (rtop) {
+#pragma unroll
+                    for (int e = 0; e < VF; ++e) rz[e] += widen<RZ, RT>(rv[q][e]) * widen<RZ, float>(xo[e]);
+                }
+                if (dst) {
+                    float so[VF];
+#pragma unroll
+                    for (int e = 0; e < VF; ++e) so[e] = sv[q][e] - w * acc[q][e];
+                    vst<float, VF>(dst + i * G + c0, so);
+                }
             }
         }
     }
-    if (rtop_base) block_partial<VF>(rz, part);
+    if (rtop_base) {
+        double rzd[VF];
+#pragma unroll
+        for (int e = 0; e < VF; ++e) rzd[e] = widen<double, RZ>(rz[e]);
+        block_partial<VF>(rzd, part);
+    }
 }
 
 // r_c = P^T s over the coarse rows (grid over the coarse depth's row blocks)
@@ -627,17 +787,35 @@ __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_prolong(Depth D, Depth C, i
 
 // s -= L y
 template <bool PC>
-__global__ void __launch_bounds__(NTB, MG_MINB_F) kb_resupdate(Depth D, float* s_base) {
+__global__ void __launch_bounds__(NTB, minb_s<PC>()) kb_resupdate(Depth D, float* s_base) {
+    constexpr int SRB = srb<PC>();
     phase_begin();
-    ROWS_F(D, t, rb, i) {
-        float* s = tv(s_base, D.n, t);
-        float acc[VF], sv[VF];
-        ell_vec_w<VF, float, float, float, PC>(D.col, tile_vals<PC>(D.L32, D, t), D.n, D.W, i, tv(D.y, D.n, t), c0,
-                                               acc);
-        vld<float, VF>(s + i * G + c0, sv);
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    if (!tile_on(D.tact, t)) return;
+    const int c0 = (threadIdx.x % TPRF) * VF;
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    float* s = tv(s_base, D.n, t);
+    const float* y = tv(D.y, D.n, t);
+    for (int i0 = rb * D.rbs + threadIdx.x / TPRF; i0 < i1; i0 += RPPF * SRB) {
+        float acc[SRB][VF], sv[SRB][VF];
 #pragma unroll
-        for (int e = 0; e < VF; ++e) sv[e] -= acc[e];
-        vst<float, VF>(s + i * G + c0, sv);
+        for (int q = 0; q < SRB; ++q) {
+            const int i = i0 + q * RPPF;
+            if (i < i1) {
+                ell_vec_w<VF, float, float, float, PC>(D.col, tile_vals<PC>(D.L32, D, t), D.n, D.W, i, y, c0, acc[q]);
+                vld<float, VF>(s + i * G + c0, sv[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < SRB; ++q) {
+            const int i = i0 + q * RPPF;
+            if (i < i1) {
+#pragma unroll
+                for (int e = 0; e < VF; ++e) sv[q][e] -= acc[q][e];
+                vst<float, VF>(s + i * G + c0, sv[q]);
+            }
+        }
     }
 }
 
@@ -908,8 +1086,9 @@ __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base,
     constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
     int t, rb;
     tile_rb(D.nrb, t, rb);
+    if (!tile_on(D.tact, t)) return;
     const int c0 = (threadIdx.x % TPR) * V;
-    double pq[V] = {};
+    T pq[V] = {};  // FP32 vectors: per-thread FP32 sums over a few rows, widened once
     T bt[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) bt[e] = (T)beta[t * G + c0 + e];
@@ -928,12 +1107,15 @@ __global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base,
         for (int e = 0; e < V; ++e) {
             pv[e] = widen<T, float>(zv[e]) + bt[e] * pv[e];
             qv[e] = lz[e] + bt[e] * qv[e];
-            pq[e] += (double)pv[e] * (double)qv[e];
+            pq[e] += pv[e] * qv[e];
         }
         vst<T, V>(p + i * G + c0, pv);
         vst<T, V>(q + i * G + c0, qv);
     }
-    block_partial<V>(pq, part);
+    double pqd[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) pqd[e] = widen<double, T>(pq[e]);
+    block_partial<V>(pqd, part);
 }
 
 // d += alpha p, r -= alpha q, partial (r, r); FP64 form: also r32 = (float) r for the V-cycle
@@ -944,8 +1126,9 @@ __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, c
     constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
     int t, rb;
     tile_rb(D.nrb, t, rb);
+    if (!tile_on(D.tact, t)) return;
     const int c0 = (threadIdx.x % TPR) * V;
-    double rr[V] = {};
+    T rr[V] = {};  // FP32 vectors: per-thread FP32 sums over a few rows, widened once
     T al[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) al[e] = (T)alpha[t * G + c0 + e];
@@ -964,7 +1147,7 @@ __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, c
         for (int e = 0; e < V; ++e) {
             dv[e] += al[e] * pv[e];
             rv[e] -= al[e] * qv[e];
-            rr[e] += (double)rv[e] * (double)rv[e];
+            rr[e] += rv[e] * rv[e];
         }
         vst<T, V>(d + i * G + c0, dv);
         vst<T, V>(r + i * G + c0, rv);
@@ -975,53 +1158,69 @@ __global__ void __launch_bounds__(NTB) kb_pcg_b(Depth D, T* d_base, T* r_base, c
             vst<float, V>(tv(r32_base, D.n, t) + i * G + c0, rf);
         }
     }
-    block_partial<V>(rr, part);
+    double rrd[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) rrd[e] = widen<double, T>(rr[e]);
+    block_partial<V>(rrd, part);
 }
 
-// FP32+refinement: r = b - L64 x for columns still refining (else 0); r32 = r, d = p = q = 0
-__global__ void __launch_bounds__(NTB) kb_refine_r(Depth D, const double* b64, const double* x64, float* r32,
-                                                   float* d32, float* p32, float* q32, const int* outer,
-                                                   double* part, double* part_ss) {
+// FP32+refinement, FP64 residual of the columns due for an update:
+// r = b - L64 (x + d) into r32, partials ||r||^2 and S^2 = || |b| + |L| |x + d| ||^2.
+// Tiles without such a column return at once.
+__global__ void __launch_bounds__(NTB) kb_ru_r(Depth D, const double* b64, const double* x64, const float* d32,
+                                               float* r32, const int* upd, double* part, double* part_ss) {
     phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
+    __shared__ int tile_any;
+    if (threadIdx.x == 0) {
+        int a = 0;
+        for (int l = 0; l < G; ++l) a |= upd[t * G + l];
+        tile_any = a;
+    }
+    __syncthreads();
+    if (!tile_any) return;
     const int lc = threadIdx.x % G, gc = t * G + lc;
-    const bool on = outer[gc] == 1;
+    const bool on = upd[gc] != 0;
     double rr[1] = {0.0}, ss[1] = {0.0};
     const double* x = tv(x64, D.n, t);
+    const float* d = tv(d32, D.n, t);
     const int i1 = min(D.n, (rb + 1) * D.rbs);
     for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
-        double ri = 0.0;
-        if (on) {
-            double lx, alx;
-            ell_row_abs<G>(D.col, D.L64, D.n, D.W, i, x, lc, lx, alx);
-            const double bi = b64[((size_t)t * D.n + i) * G + lc];
-            ri = bi - lx;
-            const double si = fabs(bi) + alx;
-            ss[0] += si * si;
+        if (!on) continue;
+        double lx = 0.0;
+        float alx = 0.0f;
+        for (int w = 0; w < D.W; ++w) {
+            const int64_t j = __ldg(D.col + w * D.n + i);
+            const double xj = x[j * G + lc] + f2d_int(d[j * G + lc]);
+            lx += __ldg(D.L64 + w * D.n + i) * xj;
+            alx += fabsf(__ldg(D.L32 + w * D.n + i)) * abs_to_float(xj);
         }
         const size_t o = ((size_t)t * D.n + i) * G + lc;
+        const double bi = b64[o];
+        const double ri = bi - lx;
         r32[o] = (float)ri;
-        d32[o] = 0.0f;
-        p32[o] = 0.0f;
-        q32[o] = 0.0f;
         rr[0] += ri * ri;
+        const float si = abs_to_float(bi) + alx;
+        ss[0] += (double)(si * si);
     }
     block_partial<1>(rr, part);
     __syncthreads();
     block_partial<1>(ss, part_ss);
 }
 
-__global__ void __launch_bounds__(NTB) kb_update_x(Depth D, double* x64, const float* d32, const int* outer) {
+// FP32+refinement: fold the FP32 correction of the updated columns into x (x += d, d = 0).
+__global__ void __launch_bounds__(NTB) kb_ru_x(Depth D, double* x64, float* d32, const int* upd) {
     phase_begin();
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
-    if (outer[gc] != 1) return;
+    if (!upd[gc]) return;
     const int i1 = min(D.n, (rb + 1) * D.rbs);
     for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
         const size_t o = ((size_t)t * D.n + i) * G + lc;
-        x64[o] += (double)d32[o];
+        x64[o] += f2d_int(d32[o]);
+        d32[o] = 0.0f;
     }
 }
 
@@ -1045,7 +1244,7 @@ struct GraphPlan {
     Cols st{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap = nullptr, cap2 = nullptr, cap3 = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;
     double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *b64 = nullptr;
     float *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     float* r32s = nullptr;  // FP64 form: FP32 shadow of the residual
@@ -1054,7 +1253,6 @@ struct GraphPlan {
         if (graph) cudaGraphDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
         if (cap2) cudaStreamDestroy(cap2);
-        if (cap3) cudaStreamDestroy(cap3);
     }
 };
 
@@ -1151,6 +1349,22 @@ void capture_precondition(GraphPlan& P, cudaStream_t s, const RT* rtop, double* 
     else capture_precondition_t<RT, false>(P, s, rtop, part);
 }
 
+// FP32+refinement: the FP64 residual update of the columns due for one, the
+// decisions taken on it (and the loop condition), then x += d for those columns
+void capture_reliable_update(GraphPlan& P, cudaStream_t s, const CallArgs* ca, cudaGraphConditionalHandle h,
+                             int use_cond) {
+    Depth& D0 = P.depth[0];
+    const size_t np = (size_t)P.ntile * D0.nrb * G;
+    double* part = P.part.as<double>();
+    double* part_rr = part + np;
+    double* part_ss = part + 2 * np;
+    pdl_launch(kb_ru_r, grid(P.ntile, D0.nrb), NTB, 0, s, D0, (const double*)P.b64, (const double*)P.x64,
+               (const float*)P.d32, P.r32, (const int*)P.st.upd, part_rr, part_ss);
+    pdl_launch(kb_scalar_ru, P.ntile, NTB, 0, s, P.st, (const double*)part_rr, (const double*)part_ss, D0.nrb, ca, h,
+               use_cond);
+    pdl_launch(kb_ru_x, grid(P.ntile, D0.nrb), NTB, 0, s, D0, P.x64, P.d32, (const int*)P.st.upd);
+}
+
 // one PCG iteration body (after the preconditioner)
 template <class T>
 void capture_pcg_body(GraphPlan& P, cudaStream_t s, T* d, T* r, T* p, T* q, const T* Lv, const CallArgs* ca,
@@ -1168,7 +1382,12 @@ void capture_pcg_body(GraphPlan& P, cudaStream_t s, T* d, T* r, T* p, T* q, cons
     pdl_launch(kb_scalar_alpha, P.ntile, NTB, 0, s, P.st, part, D0.nrb);
     pdl_launch(kb_pcg_b<T>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, d, r, p, q, P.st.alpha, part,
                                                        std::is_same<T, double>::value ? P.r32s : nullptr);
-    pdl_launch(kb_scalar_conv, P.ntile, NTB, 0, s, P.st, part, D0.nrb, ca, inner, h, use_cond);
+    if (inner) {
+        pdl_launch(kb_scalar_conv_ru, P.ntile, NTB, 0, s, P.st, part, D0.nrb, ca);
+        capture_reliable_update(P, s, ca, h, use_cond);
+    } else {
+        pdl_launch(kb_scalar_conv, P.ntile, NTB, 0, s, P.st, part, D0.nrb, ca, inner, h, use_cond);
+    }
 }
 
 // append a WHILE node at the capture's current position; returns its body graph
@@ -1280,7 +1499,7 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             P->q32 = (float*)alloc(*P, e0 * 4);
         }
         const int kpad = ntile * G;
-        P->cols.ensure((size_t)kpad * (7 * sizeof(double) + 4 * sizeof(int)) + 64);
+        P->cols.ensure((size_t)kpad * (7 * sizeof(double) + 8 * sizeof(int)) + (size_t)ntile * sizeof(int) + 64);
         char* cb = (char*)P->cols.p;
         P->st.bb = (double*)cb;
         P->st.gam = P->st.bb + kpad;
@@ -1293,14 +1512,19 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         P->st.outer = P->st.act + kpad;
         P->st.iters = P->st.outer + kpad;
         P->st.bad = P->st.iters + kpad;
-        P->st.ctr = P->st.bad + kpad;
+        P->st.upd = P->st.bad + kpad;
+        P->st.nup = P->st.upd + kpad;
+        P->st.stall = P->st.nup + kpad;
+        P->st.lastu = P->st.stall + kpad;
+        P->st.ctr = P->st.lastu + kpad;
+        P->st.tact = P->st.ctr + 16;  // after the 4 counters (padded)
+        for (auto& d : P->depth) d.tact = P->st.tact;
         const int nrb0 = P->depth[0].nrb;
         P->part.ensure((size_t)3 * ntile * std::max(nrb0, 1) * G * sizeof(double));
         P->args.ensure(sizeof(CallArgs));
         // ---- capture
         MG_CUDA(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
         MG_CUDA(cudaStreamCreateWithFlags(&P->cap2, cudaStreamNonBlocking));
-        MG_CUDA(cudaStreamCreateWithFlags(&P->cap3, cudaStreamNonBlocking));
         MG_CUDA(cudaGraphCreate(&P->graph, 0));
         cudaStream_t s = P->cap;
         MG_CUDA(cudaStreamBeginCaptureToGraph(s, P->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
@@ -1319,10 +1543,10 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             else
                 kb_init<0><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, P->r64,
                                                              P->p64, P->q64, nullptr, D0.x, part, part2, part3,
-                                                             P->r32s);
+                                                             P->r32s, nullptr, nullptr, nullptr);
             kb_scalar_init0<<<1, NSB, 0, s>>>(P->st, part, part2, P->pc ? nullptr : part3, nrb0, kpad, ca, h, 1);
             cudaGraph_t body = add_while(s, h);
-            if (!P->pc) kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
+            if (!P->pc) kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64, nullptr);
             kb_scalar_final<<<1, NSB, 0, s>>>(P->st, kpad, ca, 0, (unsigned long long*)c->counters.p,
                                               (int*)((char*)c->counters.p + 8));
             MG_CUDA(cudaStreamEndCapture(s, &P->graph));
@@ -1330,34 +1554,29 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             capture_pcg_body<double>(*P, P->cap2, P->x64, P->r64, P->p64, P->q64, D0.L64, ca, 0, h, 1);
             MG_CUDA(cudaStreamEndCapture(P->cap2, &body));
         } else {
-            cudaGraphConditionalHandle ho = new_handle(s);
+            // FP32 PCG with reliable updates: the FP32 recurrence runs on; a column whose
+            // FP32 residual has fallen by inner_tol since its last FP64 residual gets
+            // x += d and its residual replaced by b - L64 x (FP64), then continues
+            cudaGraphConditionalHandle h = new_handle(s);
             kb_init<1><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, nullptr,
                                                          nullptr, nullptr, P->b64, D0.x, part, part2, nullptr,
-                                                         nullptr);
-            kb_scalar_init1<<<1, NSB, 0, s>>>(P->st, part, nrb0, kpad, ca, ho, 1);
-            cudaGraph_t outer = add_while(s, ho);
-            kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64);
+                                                         nullptr, P->d32, P->p32, P->q32);
+            kb_scalar_init1<<<1, NSB, 0, s>>>(P->st, part, nrb0, kpad, ca);
+            capture_reliable_update(*P, s, ca, h, 1);
+            cudaGraph_t body = add_while(s, h);
+            kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64, P->d32);
             kb_scalar_final<<<1, NSB, 0, s>>>(P->st, kpad, ca, 1, (unsigned long long*)c->counters.p,
                                               (int*)((char*)c->counters.p + 8));
             MG_CUDA(cudaStreamEndCapture(s, &P->graph));
-            cudaStream_t s2 = P->cap2;
-            MG_CUDA(cudaStreamBeginCaptureToGraph(s2, outer, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-            cudaGraphConditionalHandle hi = new_handle(s2);
-            kb_refine_r<<<grid(ntile, nrb0), NTB, 0, s2>>>(D0, P->b64, P->x64, P->r32, P->d32, P->p32, P->q32,
-                                                           P->st.outer, part, part3);
-            kb_scalar_refine<<<1, NSB, 0, s2>>>(P->st, part, part3, nrb0, kpad, ca, hi, ho, 1);
-            cudaGraph_t inner = add_while(s2, hi);
-            kb_update_x<<<grid(ntile, nrb0), NTB, 0, s2>>>(D0, P->x64, P->d32, P->st.outer);
-            MG_CUDA(cudaStreamEndCapture(s2, &outer));
-            MG_CUDA(cudaStreamBeginCaptureToGraph(P->cap3, inner, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-            capture_pcg_body<float>(*P, P->cap3, P->d32, P->r32, P->p32, P->q32, D0.L32, ca, 1, hi, 1);
-            MG_CUDA(cudaStreamEndCapture(P->cap3, &inner));
+            MG_CUDA(cudaStreamBeginCaptureToGraph(P->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            capture_pcg_body<float>(*P, P->cap2, P->d32, P->r32, P->p32, P->q32, D0.L32, ca, 1, h, 1);
+            MG_CUDA(cudaStreamEndCapture(P->cap2, &body));
         }
         MG_CUDA(cudaGraphInstantiate(&P->exec, P->graph, 0));
         return P;
     } catch (...) {
         cudaStreamCaptureStatus cs;
-        for (cudaStream_t s : {P->cap, P->cap2, P->cap3})
+        for (cudaStream_t s : {P->cap, P->cap2})
             if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
                 cudaGraph_t junk = nullptr;
                 cudaStreamEndCapture(s, &junk);
@@ -1371,10 +1590,10 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
 
 }  // namespace
 
-// Profiling aid: the FP64-form kernels of the graph path launched directly on the
-// stream for a fixed number of PCG iterations (no graph, no early exit), so that
-// per-kernel profilers can see every launch.  Selected by MGRIT_EM_EAGER=<iterations>.
-static void run_eager_fp64(mg_ctx* c, GraphPlan& P, int iters) {
+// Profiling aid: the kernels of the graph path launched directly on the stream for
+// a fixed number of PCG iterations (no graph, no early exit), so that per-kernel
+// profilers can see every launch.  Selected by MGRIT_EM_EAGER=<iterations>.
+static void run_eager(mg_ctx* c, GraphPlan& P, int iters) {
     cudaStream_t s = c->stream;
     const MeshLevel& m0 = c->meshes[P.op->mesh];
     Depth& D0 = P.depth[0];
@@ -1383,14 +1602,26 @@ static void run_eager_fp64(mg_ctx* c, GraphPlan& P, int iters) {
     double* part2 = part + (size_t)P.ntile * nrb0 * G;
     double* part3 = part2 + (size_t)P.ntile * nrb0 * G;
     const CallArgs* ca = P.args.as<CallArgs>();
-    kb_init<0><<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, 1.0 / P.op->dt, m0.F.as<double>(), c->pwm.J0, P.x64, P.r64,
-                                                   P.p64, P.q64, nullptr, D0.x, part, part2, part3, P.r32s);
-    kb_scalar_init0<<<1, NSB, 0, s>>>(P.st, part, part2, part3, nrb0, kpad, ca, 0, 0);
-    for (int it = 0; it < iters; ++it)
-        capture_pcg_body<double>(P, s, P.x64, P.r64, P.p64, P.q64, D0.L64, ca, 0, 0, 0);
-    kb_final<<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, P.x64);
-    kb_scalar_final<<<1, NSB, 0, s>>>(P.st, kpad, ca, 0, (unsigned long long*)c->counters.p,
-                                      (int*)((char*)c->counters.p + 8));
+    if (P.precision == MG_FP64) {
+        kb_init<0><<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, 1.0 / P.op->dt, m0.F.as<double>(), c->pwm.J0, P.x64,
+                                                       P.r64, P.p64, P.q64, nullptr, D0.x, part, part2, part3,
+                                                       P.r32s, nullptr, nullptr, nullptr);
+        kb_scalar_init0<<<1, NSB, 0, s>>>(P.st, part, part2, part3, nrb0, kpad, ca, 0, 0);
+        for (int it = 0; it < iters; ++it)
+            capture_pcg_body<double>(P, s, P.x64, P.r64, P.p64, P.q64, D0.L64, ca, 0, 0, 0);
+        kb_final<<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, P.x64, nullptr);
+    } else {
+        kb_init<1><<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, 1.0 / P.op->dt, m0.F.as<double>(), c->pwm.J0, P.x64,
+                                                       nullptr, nullptr, nullptr, P.b64, D0.x, part, part2, nullptr,
+                                                       nullptr, P.d32, P.p32, P.q32);
+        kb_scalar_init1<<<1, NSB, 0, s>>>(P.st, part, nrb0, kpad, ca);
+        capture_reliable_update(P, s, ca, 0, 0);
+        for (int it = 0; it < iters; ++it)
+            capture_pcg_body<float>(P, s, P.d32, P.r32, P.p32, P.q32, D0.L32, ca, 1, 0, 0);
+        kb_final<<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, P.x64, P.d32);
+    }
+    kb_scalar_final<<<1, NSB, 0, s>>>(P.st, kpad, ca, P.precision == MG_FP64 ? 0 : 1,
+                                      (unsigned long long*)c->counters.p, (int*)((char*)c->counters.p + 8));
     MG_CUDA(cudaGetLastError());
 }
 
@@ -1435,7 +1666,7 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
     a.fl_acc2 = (kFloorAccept * fs) * (kFloorAccept * fs);
     MG_CUDA(cudaMemcpyAsync(P->args.p, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
     const char* eager = getenv("MGRIT_EM_EAGER");
-    if (eager && so.precision == MG_FP64) run_eager_fp64(c, *P, atoi(eager));
+    if (eager) run_eager(c, *P, atoi(eager));
     else MG_CUDA(cudaGraphLaunch(P->exec, c->stream));
     if (counters) {
         counters->step_solves += io.k;

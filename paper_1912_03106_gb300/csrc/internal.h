@@ -142,6 +142,8 @@ struct mg_ctx {
     std::string err;
     std::vector<MeshLevel> meshes;
     std::vector<std::pair<std::pair<int, int>, std::vector<int32_t>>> refinements;  // (fine, coarse) -> parent
+    // transfers given as node-space CSR matrices (mg_add_transfer): (fine, coarse) -> rows
+    std::map<std::pair<int, int>, std::vector<std::vector<std::pair<int32_t, double>>>> given_P;
     Material mats[MG_MAX_REGIONS];
     Source srcs[MG_MAX_REGIONS];
     PwmSpec pwm;
@@ -200,12 +202,18 @@ const double* ctx_find_wave_table(const mg_ctx* c, int64_t N, double T, int kind
 // up to kFloorAccept gamma S, which covers the gap between the recurrence residual
 // and the true residual that a finished solve leaves.  With the guess accepted,
 // re-solving a step from its own solution returns that solution bit for bit.
+// S is a magnitude estimate, formed in FP32 from the FP32 operator and |x| (so
+// that it costs no FP64 arithmetic); its relative error, ~1e-7, does not matter.
 inline double residual_floor(int W) {
     const double u = 1.1102230246251565e-16;  // 2^-53
     const double k = (double)(W + 1);
     return k * u / (1.0 - k * u);
 }
 constexpr double kFloorAccept = 4.0;
+// FP32+refinement: FP32 PCG iterations after which a column's FP64 residual is
+// recomputed even if its FP32 residual has not fallen by inner_tol (the FP32
+// recurrence of a stiff step stops tracking the true residual after 2-3 orders)
+constexpr int kMaxInner = 10;
 
 // Reject solver options outside their documented ranges (MG_EINVAL); every entry
 // point that runs a step calls it before any launch (mgrit.cu).
@@ -241,7 +249,8 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
                      SolveCounters* counters);
 void ctx_drop_plans(mg_ctx* c);
 // Diagnostics on stderr, from the environment variable MGRIT_EM_TRACE: 0 off,
-// 1 one line per MGRIT iteration, 2 also one line per batched Newton step.
+// 1 one line per MGRIT iteration, 2 also one line per batched Newton step, 3 also
+// one line per autotuner trial (each trial then synchronises the stream).
 int mg_trace_level();
 // column bucket of the autotuner's table: k itself up to 16, else whole 16-column tiles
 inline int tune_bucket(int k) { return k <= 16 ? k : (k + 15) / 16 * 16; }

@@ -695,11 +695,13 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
     bool converged = false;
     // inexact step solves: tolerance proportional to the current relative residual
     const bool adaptive = o.step_tol_ratio > 0.0 && o.stop_rule == 0;
-    const double tol_cg = o.solver.cg_tol, tol_ref = o.solver.refine_tol;
+    const double tol_cg = o.solver.cg_tol, tol_ref = o.solver.refine_tol, tol_newton = o.solver.newton_tol;
     auto set_step_tol = [&](double rho) {
         if (!adaptive) return;
         S.o.solver.cg_tol = std::max(tol_cg, o.step_tol_ratio * rho);
         S.o.solver.refine_tol = std::max(tol_ref, o.step_tol_ratio * rho);
+        // Newton steps: the relative update at which Newton stops
+        S.o.solver.newton_tol = std::max(tol_newton, o.step_tol_ratio * rho);
     };
     set_step_tol(1.0);
     // stagnation (residual rule only): for kStallIters iterations in a row no residual
@@ -790,7 +792,7 @@ void mg_solver_defaults(mg_solver_opts* s) {
     std::memset(s, 0, sizeof(*s));
     s->cg_tol = 1e-13;
     s->refine_tol = 1e-13;
-    s->inner_tol = 1e-5;
+    s->inner_tol = 3e-2;
     s->max_cg = 2000;
     s->max_refine = 30;
     s->precision = MG_FP64;

@@ -135,6 +135,10 @@ struct Smem {
     int outer[KT];
     int iters[KT];
     int bad[KT];  // a non-finite residual or right-hand side was seen
+    int upd[KT];    // FP32+refine: FP64 residual update due
+    int nup[KT];    // FP32+refine: FP64 residual updates done
+    int stall[KT];  // FP32+refine: updates in a row that took less than 10 % off ||r||
+    int lastu[KT];  // FP32+refine: the column's iteration count at its last FP64 update
     int any;
 };
 
@@ -732,6 +736,156 @@ __device__ void pcg(Ctx<KT>& c, Smem<KT>& s, const PcgArgs& a, T* d, T* r, T* p,
     }
 }
 
+// FP32+refinement: FP64 residual update of the columns with s.upd set:
+// r = b - L64 (x + d) into r32, then the column's decisions (stop at the tolerance
+// or the rounding floor, fail when not finite, after max_refine updates or three
+// updates in a row that took less than 10 % off ||r|| above the acceptance margin), then
+// x += d, d = 0 for those columns.  Called by every thread of the cluster.
+template <int KT>
+__device__ void reliable_update(Ctx<KT>& c, Smem<KT>& s, const PcgArgs& a) {
+    const DepthArgs& D = a.d[0];
+    const int lc = threadIdx.x % KT;
+    const int64_t rs = NT / KT;
+    int64_t rb0, re0;
+    c.rows(D.n, rb0, re0);
+    double* x64 = c.tv(a.x64, D.n);
+    const double* b64 = c.tv(a.b64, D.n);
+    float* d32 = c.tv(a.d32, D.n);
+    float* r32 = c.tv(a.r32, D.n);
+    const bool on = s.upd[lc] != 0;
+    double v[2][1] = {{0.0}, {0.0}};
+    for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
+        if (!on) continue;
+        double lx = 0.0;
+        float alx = 0.0f;
+        for (int w = 0; w < D.W; ++w) {
+            const int64_t j = __ldg(D.col + (int64_t)w * D.n + i);
+            const double xj = ldcg(x64 + j * KT + lc) + (double)ldcg(d32 + j * KT + lc);
+            lx += __ldg(D.L64 + (int64_t)w * D.n + i) * xj;
+            alx += fabsf(__ldg(D.L32 + (int64_t)w * D.n + i)) * abs_to_float(xj);
+        }
+        const double bi = ldcg(b64 + i * KT + lc);
+        const double ri = bi - lx;
+        stcg(r32 + i * KT + lc, (float)ri);
+        v[0][0] += ri * ri;
+        const float si = abs_to_float(bi) + alx;
+        v[1][0] += (double)(si * si);
+    }
+    cluster_sum<KT, 1, 2, double>(c, s, v);  // its cluster barrier also ends all reads of x and d
+    if (threadIdx.x < KT) {
+        const int cc = threadIdx.x;
+        if (s.upd[cc] && s.outer[cc] == 1) {
+            const double rr = s.tot[0][cc], sv = s.tot[1][cc];
+            const bool first = s.nup[cc] == 0;
+            const double fl2 = first ? a.fl_acc2 : a.fl_stop2;
+            if (!(rr - rr == 0.0)) {
+                s.bad[cc] = 1;
+                s.outer[cc] = 2;
+            } else if (rr <= a.tol * a.tol * s.bb[cc] || rr <= fl2 * sv) {
+                s.outer[cc] = 0;
+            } else {
+                if (!first && rr > 0.81 * s.ref[cc]) s.stall[cc] += 1;
+                else s.stall[cc] = 0;
+                if (s.stall[cc] >= 3) s.outer[cc] = rr <= a.fl_acc2 * sv ? 0 : 2;
+                else if (s.nup[cc] > a.max_refine) s.outer[cc] = 2;
+            }
+            // the FP32 recurrence had drifted from the true residual by more than 2x:
+            // its search direction no longer fits, restart it (beta = 0)
+            if (!first && rr > 4.0 * s.prev[cc]) s.gam[cc] = 0.0;
+            s.nup[cc] += 1;
+            s.ref[cc] = rr;
+            s.lastu[cc] = s.iters[cc];
+            s.act[cc] = s.outer[cc] == 1;
+        }
+    }
+    for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
+        if (!on) continue;
+        const int64_t o = i * KT + lc;
+        stcg(x64 + o, ldcg(x64 + o) + (double)ldcg(d32 + o));
+        stcg(d32 + o, 0.0f);
+    }
+    update_any(s);
+}
+
+// FP32 PCG with reliable updates (FP32+refinement form): the FP32 recurrence runs
+// on across FP64 residual replacements; a column whose FP32 residual has fallen by
+// inner_tol since its last FP64 residual, or below the tolerance, is updated.
+template <int KT>
+__device__ void pcg_ru(Ctx<KT>& c, Smem<KT>& s, const PcgArgs& a, float* stage) {
+    constexpr int VF = vf(KT);
+    const DepthArgs& D = a.d[0];
+    float* d = c.tv(a.d32, D.n);
+    float* r = c.tv(a.r32, D.n);
+    float* p = c.tv(a.p32, D.n);
+    float* q = c.tv(a.q32, D.n);
+    const float* z = c.tv(D.x, D.n);
+    if (threadIdx.x < KT) {
+        s.upd[threadIdx.x] = s.outer[threadIdx.x] == 1;
+        s.beta[threadIdx.x] = 0.0;
+    }
+    __syncthreads();
+    reliable_update<KT>(c, s, a);
+    for (int it = 1; it <= a.max_it && s.any; ++it) {
+        {
+            double rz[1][VF] = {};
+            precondition<KT, float>(c, a, (const float*)r, stage, rz[0]);
+            cluster_sum<KT, VF, 1, double>(c, s, rz);
+            if (threadIdx.x < KT) {
+                int cc = threadIdx.x;
+                double gn = s.tot[0][cc];
+                s.beta[cc] = (it == 1 || s.gam[cc] == 0.0) ? 0.0 : gn / s.gam[cc];
+                s.gam[cc] = gn;
+            }
+            __syncthreads();
+        }
+        {
+            PhPcgA<KT, VF, float> ph{D, D.L32, z, p, q, s.beta, Lanes<KT, VF>::c0(), {}, {}, {}, {}, {}};
+            run_rows<KT, VF>(c, D.n, ph);
+            double v[1][VF];
+#pragma unroll
+            for (int e = 0; e < VF; ++e) v[0][e] = ph.pq[e];
+            cluster_sum<KT, VF, 1, double>(c, s, v);
+            if (threadIdx.x < KT) {
+                int cc = threadIdx.x;
+                double pq = s.tot[0][cc];
+                s.alpha[cc] = (s.act[cc] && pq != 0.0) ? s.gam[cc] / pq : 0.0;
+            }
+            __syncthreads();
+        }
+        {
+            PhPcgB<KT, VF, float> ph{d, r, p, q, s.alpha, Lanes<KT, VF>::c0(), {}, {}, {}, {}, {}};
+            run_rows<KT, VF>(c, D.n, ph);
+            double v[1][VF];
+#pragma unroll
+            for (int e = 0; e < VF; ++e) v[0][e] = ph.rr[e];
+            cluster_sum<KT, VF, 1, double>(c, s, v);
+            if (threadIdx.x < KT) {
+                int cc = threadIdx.x;
+                int u = 0;
+                if (s.act[cc]) {
+                    s.iters[cc] = it;
+                    const double rr = s.tot[0][cc];
+                    if (!(rr - rr == 0.0)) {
+                        s.bad[cc] = 1;
+                        s.act[cc] = 0;
+                        s.outer[cc] = 2;
+                    } else {
+                        u = rr <= a.inner_tol * a.inner_tol * s.ref[cc] || rr <= a.tol * a.tol * s.bb[cc] ||
+                            s.iters[cc] - s.lastu[cc] >= kMaxInner;
+                        if (u) s.prev[cc] = rr;  // the FP32 residual the FP64 one is compared with
+                    }
+                }
+                s.upd[cc] = u;
+            }
+            __syncthreads();
+            int anyu = 0;
+            for (int cc = 0; cc < KT; ++cc) anyu |= s.upd[cc];
+            if (anyu) reliable_update<KT>(c, s, a);
+            else update_any(s);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- the kernel
 template <int KT, int MODE>
 __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
@@ -772,7 +926,8 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
         double* b64 = a.mode == 1 ? c.tv(a.b64, D.n) : nullptr;
         float* z = c.tv(D.x, D.n);
         for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
-            double bi = 0.0, lx = 0.0, xi = 0.0, alx = 0.0;
+            double bi = 0.0, lx = 0.0, xi = 0.0;
+            float alx = 0.0f;  // sum |L_ij| |x_j| of the rounding floor (an estimate: FP32)
             if (valid) {
                 double mb = 0.0;
                 for (int wq = 0; wq < D.W; ++wq) {
@@ -781,9 +936,8 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
                     if (a.guess) {
                         double xj = a.guess[j * a.ld_guess + cio];
                         if (a.g) xj -= a.g[j * a.ld_g + cio];
-                        const double lv = __ldg(D.L64 + (int64_t)wq * D.n + i);
-                        lx += lv * xj;
-                        alx += fabs(lv) * fabs(xj);
+                        lx += __ldg(D.L64 + (int64_t)wq * D.n + i) * xj;
+                        alx += fabsf(__ldg(D.L32 + (int64_t)wq * D.n + i)) * abs_to_float(xj);
                     }
                 }
                 bi = mb * a.inv_dt + a.J0 * (sg[0] * a.F[i] + sg[1] * a.F[D.n + i] + sg[2] * a.F[2 * D.n + i]);
@@ -803,8 +957,8 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
                 stcg(b64 + o, bi);
             }
             v[0][0] += bi * bi;
-            const double si = fabs(bi) + alx;
-            v[1][0] += si * si;
+            const float si = abs_to_float(bi) + alx;
+            v[1][0] += (double)(si * si);
         }
         cluster_sum<KT, 1, 2, double>(c, s, v);
         if (threadIdx.x < KT) {
@@ -821,73 +975,28 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
         if (threadIdx.x < KT) s.outer[threadIdx.x] = s.act[threadIdx.x];
         __syncthreads();
     } else {
-        int total_it = 0;
-        const double* b64 = c.tv(a.b64, D.n);
-        float* r32 = c.tv(a.r32, D.n);
-        float* d32 = c.tv(a.d32, D.n);
-        float* p32 = c.tv(a.p32, D.n);
-        float* q32 = c.tv(a.q32, D.n);
-        for (int sweep = 0; sweep <= a.max_refine; ++sweep) {
-            // ---- r = b - L64 x (FP64) and S^2 of its rounding floor; inner start d = 0, r32 = r
-            double v[2][1] = {{0.0}, {0.0}};
-            for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
-                double ri = 0.0;
-                if (s.outer[lc] == 1) {
-                    double lx, alx;
-                    ell_row_abs<KT>(D.col, D.L64, D.n, D.W, (int)i, (const double*)x64, lc, lx, alx);
-                    const double bi = ldcg(b64 + i * KT + lc);
-                    ri = bi - lx;
-                    const double si = fabs(bi) + alx;
-                    v[1][0] += si * si;
-                }
-                const int64_t o = i * KT + lc;
-                stcg(r32 + o, (float)ri);
-                stcg(d32 + o, 0.0f);
-                stcg(p32 + o, 0.0f);
-                stcg(q32 + o, 0.0f);
-                v[0][0] += ri * ri;
-            }
-            cluster_sum<KT, 1, 2, double>(c, s, v);
-            if (threadIdx.x < KT) {
-                int cc = threadIdx.x;
-                double rr = s.tot[0][cc];
-                if (s.outer[cc] == 1) {
-                    // done: tolerance met or x solves the step to working precision, or the
-                    // FP64 residual no longer halves, accepted once it is below 1e-8 ||b||
-                    const double fl2 = sweep == 0 ? a.fl_acc2 : a.fl_stop2;
-                    const bool met = rr <= a.tol * a.tol * s.bb[cc] || rr <= fl2 * s.tot[1][cc];
-                    const bool stalled = sweep > 0 && rr > 0.25 * s.prev[cc];
-                    if (met || (stalled && rr <= 1e-16 * s.bb[cc])) s.outer[cc] = 0;
-                    else if (stalled || sweep == a.max_refine || !(rr - rr == 0.0)) s.outer[cc] = 2;
-                    if (!(rr - rr == 0.0)) s.bad[cc] = 1;
-                }
-                s.act[cc] = s.outer[cc] == 1;
-                s.ref[cc] = rr;
-                s.prev[cc] = rr;
-            }
-            update_any(s);
-            if (!s.any) break;
-            pcg<KT, float>(c, s, a, a.d32, a.r32, a.p32, a.q32, D.L32, a.inner_tol * a.inner_tol, 0.0, 0.0, stage);
-            if (threadIdx.x == 0) {
-                int mx = 0;
-                for (int cc = 0; cc < KT; ++cc) mx = max(mx, s.iters[cc]);
-                total_it += mx;
-            }
-            // ---- x += d (d is zero for columns not refined in this sweep)
-            for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
-                const int64_t o = i * KT + lc;
-                if (s.outer[lc] == 1) stcg(x64 + o, ldcg(x64 + o) + (double)ldcg(d32 + o));
-            }
-            c.cl.sync();
+        // d = p = q = 0 (the initial FP64 residual comes from the first update)
+        for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
+            const int64_t o = i * KT + lc;
+            stcg(c.tv(a.d32, D.n) + o, 0.0f);
+            stcg(c.tv(a.p32, D.n) + o, 0.0f);
+            stcg(c.tv(a.q32, D.n) + o, 0.0f);
         }
-        if (threadIdx.x == 0) s.iters[0] = total_it;
-        __syncthreads();
+        if (threadIdx.x < KT) {
+            s.nup[threadIdx.x] = 0;
+            s.stall[threadIdx.x] = 0;
+            s.lastu[threadIdx.x] = 0;
+        }
+        c.cl.sync();
+        pcg_ru<KT>(c, s, a, stage);
     }
 
-    // ---- x_out = x + g; per-column status
+    // ---- x_out = x (+ d not yet folded in) + g; per-column status
+    c.cl.sync();
     if (valid) {
         for (int64_t i = rb0 + threadIdx.x / KT; i < re0; i += rs) {
             double xi = ldcg(x64 + i * KT + lc);
+            if (a.mode == 1) xi += (double)ldcg(c.tv(a.d32, D.n) + i * KT + lc);
             if (a.g) xi += a.g[i * a.ld_g + cio];
             a.xout[i * a.ld_out + cio] = xi;
         }
@@ -896,7 +1005,7 @@ __global__ void __launch_bounds__(NT, MG_MINB) k_phi_batch(PcgArgs a) {
         int cc = threadIdx.x;
         if (s.bad[cc]) atomicMin(a.worst, (int)MG_ENONFINITE);
         else if (s.outer[cc]) atomicMin(a.worst, (int)MG_ECG_MAXIT);
-        atomicAdd(a.iter_sum, (unsigned long long)(a.mode == 0 ? s.iters[cc] : (cc == 0 ? s.iters[0] : 0)));
+        atomicAdd(a.iter_sum, (unsigned long long)s.iters[cc]);
     }
 }
 
@@ -966,6 +1075,12 @@ static int choose_tile(int k, int want) {
 
 void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so, SolveCounters* counters) {
     if (io.k <= 0) return;
+    // the kernels add their PCG iterations and statuses to the context counters;
+    // a caller that did not reset them (the autotuner) may come first
+    if (!c->counters.p) {
+        c->counters.ensure(16);
+        MG_CUDA(cudaMemsetAsync(c->counters.p, 0, 16, c->stream));
+    }
     if (so.max_cg < 1 || so.max_refine < 0 || (so.precision != MG_FP64 && so.precision != MG_FP32_REFINE) ||
         (so.precond != MG_PRECOND_JACOBI && so.precond != MG_PRECOND_MULTIGRID))
         mg_fail(MG_EINVAL, "bad solver options");

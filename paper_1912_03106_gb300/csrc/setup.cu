@@ -696,11 +696,12 @@ Transfer& ctx_transfer(mg_ctx* c, int fine, int coarse) {
     auto key = std::make_pair(fine, coarse);
     auto it = c->transfers.find(key);
     if (it != c->transfers.end()) return *it->second;
-    // chain of refinements fine -> ... -> coarse
+    // a transfer given by the caller, or the chain of refinements fine -> ... -> coarse
+    auto given = c->given_P.find(key);
     std::vector<const std::vector<int32_t>*> chain;
     std::vector<int> path{fine};
     int cur = fine;
-    while (cur != coarse) {
+    while (given == c->given_P.end() && cur != coarse) {
         const std::vector<int32_t>* par = nullptr;
         int nxt = -1;
         for (auto& r : c->refinements)
@@ -715,7 +716,8 @@ Transfer& ctx_transfer(mg_ctx* c, int fine, int coarse) {
     const MeshLevel& mf = c->meshes[fine];
     const MeshLevel& mc = c->meshes[coarse];
     // compose node-space rows: P = P_1 P_2 ... (fine first)
-    std::vector<Row> P = one_refinement(*chain[0], c->meshes[path[0]].n_nodes);
+    std::vector<Row> P = given != c->given_P.end() ? given->second
+                                                    : one_refinement(*chain[0], c->meshes[path[0]].n_nodes);
     for (size_t k = 1; k < chain.size(); ++k) {
         std::vector<Row> Pk = one_refinement(*chain[k], c->meshes[path[k]].n_nodes);
         for (auto& row : P) {
@@ -758,9 +760,19 @@ Transfer& ctx_transfer(mg_ctx* c, int fine, int coarse) {
         for (int32_t q = tp[cd]; q < tp[cd + 1]; ++q) rowsum[cd] += tv[q];
     std::vector<double> rinv(mc.n);
     for (int64_t cd = 0; cd < mc.n; ++cd) rinv[cd] = 1.0 / rowsum[cd];
-    // injection: fine node coinciding with each coarse node
+    // injection: fine node coinciding with each coarse node (a given transfer: the
+    // fine node whose row of P is the coarse node's unit vector)
     std::vector<int32_t> inj(mc.n, -1);
-    {
+    if (given != c->given_P.end()) {
+        std::vector<int32_t> at(mc.n_nodes, -1);
+        for (int64_t i = 0; i < mf.n_nodes; ++i)
+            if (P[i].size() == 1 && P[i][0].second == 1.0) at[P[i][0].first] = (int32_t)i;
+        for (int64_t cd = 0; cd < mc.n; ++cd) {
+            const int32_t fnode = at[mc.dof2node[cd]];
+            if (fnode < 0 || mf.node2dof[fnode] < 0) mg_fail(MG_EINVAL, "coarse node without a fine interior node");
+            inj[cd] = mf.node2dof[fnode];
+        }
+    } else {
         std::vector<int32_t> node(mc.n_nodes);
         std::iota(node.begin(), node.end(), 0);
         for (int k = (int)chain.size() - 1; k >= 0; --k) {
@@ -882,6 +894,39 @@ mg_status mg_add_refinement(mg_ctx* c, int fine, int coarse, const int32_t* pare
         for (auto& r : c->refinements)
             if (r.first.first == fine) mg_fail(MG_EINVAL, "mesh already has a coarse parent");
         c->refinements.push_back({{fine, coarse}, std::move(par)});
+    });
+}
+
+mg_status mg_add_transfer(mg_ctx* c, int fine, int coarse, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                          const double* val) {
+    return guarded(c, [&] {
+        if (fine < 0 || coarse < 0 || fine >= (int)c->meshes.size() || coarse >= (int)c->meshes.size() ||
+            fine == coarse || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val)))
+            mg_fail(MG_EINVAL, "mg_add_transfer: bad arguments");
+        const int64_t nf = c->meshes[fine].n_nodes, nc = c->meshes[coarse].n_nodes;
+        if (rowptr[0] != 0 || rowptr[nf] != nnz) mg_fail(MG_EINVAL, "mg_add_transfer: rowptr must run from 0 to nnz");
+        std::vector<Row> P(nf);
+        std::vector<int32_t> unit_at(nc, -1);
+        for (int64_t i = 0; i < nf; ++i) {
+            if (rowptr[i + 1] < rowptr[i]) mg_fail(MG_EINVAL, "mg_add_transfer: rowptr must not decrease");
+            for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+                if (col[q] < 0 || col[q] >= nc) mg_fail(MG_EINVAL, "mg_add_transfer: column out of range");
+                if (!std::isfinite(val[q])) mg_fail(MG_EINVAL, "mg_add_transfer: value not finite");
+                P[i].push_back({col[q], val[q]});
+            }
+            if (P[i].size() == 1 && P[i][0].second == 1.0) unit_at[P[i][0].first] = (int32_t)i;
+        }
+        // nodal interpolation between nested node sets: every coarse node is a fine node
+        for (int64_t j = 0; j < nc; ++j)
+            if (unit_at[j] < 0)
+                mg_fail(MG_EINVAL, "mg_add_transfer: coarse node " + std::to_string(j) +
+                                       " has no fine node whose row of P is its unit vector");
+        c->given_P[{fine, coarse}] = std::move(P);
+        auto it = c->transfers.find({fine, coarse});  // a transfer built before is rebuilt from this one
+        if (it != c->transfers.end()) {
+            delete it->second;
+            c->transfers.erase(it);
+        }
     });
 }
 

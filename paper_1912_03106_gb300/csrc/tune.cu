@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <limits>
 #include <vector>
@@ -87,7 +88,13 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
                 so.rows_per_block = t.rbs0;
                 so.coarse_rows_per_block = t.rbs1;
                 so.base_tiles = t.tb;
+                if (mg_trace_level() >= 3) {
+                    std::fprintf(stderr, "[autotune] mesh %d k %d path %d tile %d cluster %d rbs %d/%d tiles %d\n",
+                                 A.level, A.k, t.path, t.tile, t.cluster, t.rbs0, t.rbs1, t.tb);
+                    MG_CUDA(cudaStreamSynchronize(s));
+                }
                 phi_batch(c, op, io, so, nullptr);  // builds the plan, warms the caches
+                if (mg_trace_level() >= 3) MG_CUDA(cudaStreamSynchronize(s));
                 MG_CUDA(cudaEventRecord(e0, s));
                 for (int r = 0; r < 3; ++r) phi_batch(c, op, io, so, nullptr);
                 MG_CUDA(cudaEventRecord(e1, s));

@@ -106,19 +106,16 @@ __device__ __forceinline__ void ell_vec(const int32_t* __restrict__ col, const V
     }
 }
 
-// One row of the FP64 residual product with the magnitude sum needed for its
-// rounding bound: acc = sum_w val[w, i] v[col[w, i]][c], aacc = sum_w |val| |v|.
-template <int KT>
-__device__ __forceinline__ void ell_row_abs(const int32_t* __restrict__ col, const double* __restrict__ val, int n,
-                                            int W, int i, const double* v, int c, double& acc, double& aacc) {
-    acc = 0.0;
-    aacc = 0.0;
-    for (int w = 0; w < W; ++w) {
-        const double a = __ldg(val + w * n + i);
-        const double x = __ldcg(v + (int64_t)__ldg(col + w * n + i) * KT + c);
-        acc += a * x;
-        aacc += fabs(a) * fabs(x);
-    }
+// |x| as a float, by integer instructions (exponent rebiased, mantissa truncated:
+// at most 2^-23 below |x|; 0 below the float range, infinity above it).  Used for
+// magnitude estimates, which need no FP64 arithmetic: on GB300 the FP64 pipe, which
+// also converts between double and float, runs at a small fraction of FP32's rate.
+__device__ __forceinline__ float abs_to_float(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    const int e = (int)(u >> 52) - 1023 + 127;
+    if (e <= 0) return 0.0f;
+    if (e >= 255) return __uint_as_float(0x7f800000u);
+    return __uint_as_float(((unsigned)e << 23) | (unsigned)((u >> 29) & 0x7fffffull));
 }
 
 }  // namespace mgv

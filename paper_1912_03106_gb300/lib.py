@@ -103,6 +103,7 @@ _SIGNATURES = {
     "mg_set_stream": (C.c_int, [_P, _P]),
     "mg_add_mesh": (C.c_int, [_P, C.POINTER(C.c_int), _I64, _P, _I64, _P, _P, _I64, _P]),
     "mg_add_refinement": (C.c_int, [_P, C.c_int, C.c_int, _P]),
+    "mg_add_transfer": (C.c_int, [_P, C.c_int, C.c_int, C.c_int64, _P, _P, _P]),
     "mg_set_material": (C.c_int, [_P, C.c_int32, _D, _D, C.c_int, _D, _D, _D]),
     "mg_set_source": (C.c_int, [_P, C.c_int32, C.c_int, C.c_int]),
     "mg_set_pwm": (C.c_int, [_P, _D, _D, _D, C.c_int, _D]),

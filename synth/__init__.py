@@ -11,6 +11,7 @@ from .annulus import (  # noqa: F401
     Mesh,
     annulus_mesh,
     refine,
+    barycentric_split,
     mesh_hierarchy,
     REGION_ROTOR,
     REGION_GAP,

@@ -80,7 +80,10 @@ class Mesh:
         return np.concatenate([inner, outer])
 
     def interior_nodes(self) -> np.ndarray:
-        return np.arange(self.nth, self.nr * self.nth, dtype=np.int32)
+        """All nodes but the Dirichlet ones, in increasing order."""
+        keep = np.ones(self.n_nodes, dtype=bool)
+        keep[self.dirichlet_nodes()] = False
+        return np.nonzero(keep)[0].astype(np.int32)
 
 
 def _triangles(nr: int, nth: int) -> np.ndarray:
@@ -168,6 +171,31 @@ def refine(m: Mesh) -> Mesh:
     parent_e = 2 * ((Iq // 2) * nth + (Jq // 2)) + parent_upper
     region = m.region[parent_e].astype(np.int32)
     return Mesh(xy=xy, tri=tri, region=region, nr=NR, nth=NTH, parent=parent)
+
+
+def barycentric_split(m: Mesh) -> tuple[Mesh, np.ndarray]:
+    """Each triangle split into three at its centroid: a mesh nested in m (every
+    node of m is a node of it, every triangle of m the union of three of its
+    triangles) that red refinement does not produce.
+
+    Returns (mesh, parents).  The nodes of m keep their numbers; the centroid of
+    triangle e is node m.n_nodes + e.  Triangle e's children (a, b, c), (b, d, c),
+    (d, a, c) for e = (a, b, d) with centroid c are numbered e, n_tri + e,
+    2 n_tri + e and inherit its region.  nr, nth still describe the logical grid
+    of m, so the Dirichlet nodes are unchanged (no centroid lies on a circle);
+    `parent` is None (not a red refinement).  parents (n_nodes, 3) int32 lists for
+    each node the nodes of m it lies on: (p, p, p) for node p of m, the three
+    vertices of e for the centroid of e.
+    """
+    n = m.n_nodes
+    xy = np.vstack([m.xy, m.xy[m.tri].mean(axis=1)])
+    c = (n + np.arange(m.n_tri)).astype(np.int32)
+    a, b, d = m.tri[:, 0], m.tri[:, 1], m.tri[:, 2]
+    tri = np.concatenate([np.stack([a, b, c], axis=1), np.stack([b, d, c], axis=1),
+                          np.stack([d, a, c], axis=1)]).astype(np.int32)
+    region = np.tile(m.region, 3).astype(np.int32)
+    parents = np.vstack([np.repeat(np.arange(n, dtype=np.int32)[:, None], 3, axis=1), m.tri]).astype(np.int32)
+    return Mesh(xy=xy, tri=tri, region=region, nr=m.nr, nth=m.nth, parent=None), parents
 
 
 def mesh_hierarchy(levels: int = 4, nr: int = 24, nth: int = 48, jitter: float = 0.1,

@@ -6,7 +6,9 @@ import pytest
 
 import synth
 from synth.model import PwmSpec, machine_model
-from synth.workloads import instances
+from synth.workloads import Instance, instances
+from oracle import fem, pwm as opwm, stepper
+from oracle.problem import MachineProblem, rel_err_per_point
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -30,10 +32,13 @@ def make_ctx(meshes, model, stream=None):
 
 @pytest.mark.parametrize("level,k", [(2, 256), (0, 16), (0, 1)])
 def test_autotune_shape_gives_the_same_step(meshes, level, k):
+    """The tuned launch shape solves the step as the oracle does (banded Cholesky),
+    to the bar of the other FP64 step tests, and equals the default shape's step."""
     model = machine_model(pwm=PwmSpec(J0=1e6, f_carrier=20e3))
     ctx, ids = make_ctx(meshes, model)
     n = ctx.mg_num_dofs(ids[level])
-    x = torch.as_tensor(0.01 * np.random.default_rng(k).standard_normal((n, k)), device="cuda")
+    xn = 0.01 * np.random.default_rng(k).standard_normal((n, k))
+    x = torch.as_tensor(xn, device="cuda")
     ref = torch.zeros_like(x)
     ctx.mg_step(ids[level], 4096, 20e-3, x, ref, i0=1, istride=1 if k > 1 else 0)
     so, ms = ctx.mg_autotune(ids[level], 4096, 20e-3, k)
@@ -44,10 +49,27 @@ def test_autotune_shape_gives_the_same_step(meshes, level, k):
     ctx.mg_step(ids[level], 4096, 20e-3, x, got, i0=1, istride=1 if k > 1 else 0, solver=so)
     err = ((got - ref).norm(dim=0) / ref.norm(dim=0)).max().item()
     assert err <= 1e-11, err
+    fe = fem.FEModel(meshes[level], model)
+    phi = stepper.LinearPhi(fe, 20e-3 / 4096, stepper.Forcing(fe.F, model.pwm.J0,
+                                                             opwm.sign_table(model.pwm, 20e-3, 4096), 1))
+    g = got.cpu().numpy()
+    for c in sorted({0, k // 2, k - 1}):
+        want = phi(xn[:, c], 1 + c if k > 1 else 1)
+        assert np.linalg.norm(g[:, c] - want) <= 1e-10 * np.linalg.norm(want), c
     # default options now pick the recorded shape: identical to the explicit run
     again = torch.zeros_like(x)
     ctx.mg_step(ids[level], 4096, 20e-3, x, again, i0=1, istride=1 if k > 1 else 0)
     assert torch.equal(again, got)
+    ctx.close()
+
+
+def test_autotune_of_single_steps_first_on_a_fresh_context(meshes):
+    """The autotuner's first trials on a new context run the cluster path before any
+    solve has set up the context's iteration counters: they must be set up there."""
+    model = machine_model(pwm=PwmSpec(J0=1e6, f_carrier=20e3))
+    ctx, ids = make_ctx(meshes, model)
+    so, ms = ctx.mg_autotune(ids[2], 4096, 20e-3, 1)
+    assert ms > 0.0 and so.path in (1, 2)
     ctx.close()
 
 
@@ -96,6 +118,33 @@ def test_batch_solve_equals_one_by_one(meshes):
     assert all(s["iters"] >= 1 for s in stats)
 
 
+def test_batch_solve_matches_oracle(meshes):
+    """Instances solved together by mg_batch_solve, each against the oracle's
+    sequential stepping: FP64 and FP32+refinement linear instances on the
+    1,104- and 4,512-DOF meshes, a Brauer-law instance with Newton steps."""
+    insts = [Instance(0, 64, 2.5e-3, 5e3, 1.0e6, False), Instance(1, 128, 5e-3, 20e3, 2.0e6, False),
+             Instance(1, 64, 2.5e-3, 10e3, 0.7e6, False), Instance(0, 32, 1.25e-3, 20e3, 3.0e6, True)]
+    precision = [0, 1, 0, 0]
+    streams = [torch.cuda.Stream() for _ in insts]
+    setups = []
+    for inst, s, p in zip(insts, streams, precision):
+        ctx, opts, a0, out = instance_setup(meshes, inst, s)
+        opts.tol = 1e-10 if inst.nonlinear else 1e-11
+        opts.solver.precision = p
+        setups.append((ctx, opts, a0, out))
+    torch.cuda.synchronize()
+    rc, status, stats = api.mg_batch_solve([s[0] for s in setups], [i.N for i in insts], [i.T for i in insts],
+                                           [s[2] for s in setups], [s[3] for s in setups], [s[1] for s in setups])
+    assert rc == 0, status
+    for (ctx, opts, a0, out), inst, p in zip(setups, insts, precision):
+        model = machine_model(nonlinear=inst.nonlinear, pwm=PwmSpec(J0=inst.J0, f_carrier=inst.f_carrier))
+        ref = MachineProblem(meshes, model, inst.N, inst.T, (inst.mesh_level,), (),
+                             nonlinear=inst.nonlinear).sequential()
+        err = rel_err_per_point(out.cpu().numpy(), ref).max()
+        assert err <= (1e-6 if p else 1e-9 if inst.nonlinear else 1e-10), (inst, err)
+        ctx.close()
+
+
 def test_batch_solve_rejects_repeated_context(meshes):
     inst = instances(1, seed=0, mesh_levels=(0,), Ns=(64,), T=2.5e-3, nonlinear_fraction=0.0)[0]
     ctx, opts, a0, out = instance_setup(meshes, inst, torch.cuda.Stream())
@@ -127,6 +176,12 @@ def test_plan_levels_gives_a_converging_hierarchy(meshes):
     assert rc == 0, st["res_hist"]
     err = ((out[1:] - seq[1:]).norm(dim=1) / seq[1:].norm(dim=1)).max().item()
     assert err <= 1e-5, err
+    # the oracle's sequential stepping at sampled time points
+    fe = fem.FEModel(meshes[2], model)
+    phi = stepper.LinearPhi(fe, T / N, stepper.Forcing(fe.F, model.pwm.J0, opwm.sign_table(model.pwm, T, N), 1))
+    ref = stepper.sequential(phi, 1024, np.zeros(n))
+    got = out[:1025].cpu().numpy()
+    assert rel_err_per_point(got, ref).max() <= 1e-5
     print("plan", opts.levels, [opts.m[l] for l in range(opts.levels - 1)], "est ms/iter", est,
           "iters", st["iters"], "solve s", st["t_solve"])
     ctx.close()
