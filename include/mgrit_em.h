@@ -384,12 +384,16 @@ mg_status mg_choose_levels(const double* k_list, const double* ms_list, int nk, 
                            int* levels_out, int* m_out);
 
 /* Measures batched-step times on mesh fine_level for 16, 32, ..., 1024 columns
- * (at most N/2), applies mg_choose_levels, and fills opts->levels, opts->m and
+ * (at most N/2) and applies mg_choose_levels; then runs 4 MGRIT iterations (from
+ * a0 = 0, the other fields of *opts kept) of that plan and of fixed hierarchies
+ * (m = 16; 16 x 16; 32 x 16; 8 x 8 x 8 -- those that divide N and fit max_levels)
+ * and chooses the one with the least predicted time to opts->tol: measured time
+ * per iteration times the iterations that the measured residual reduction per
+ * iteration (after the first) needs.  Fills opts->levels, opts->m and
  * opts->space_level (fine_level on the finest time level, coarse_level on the
- * others; its other fields are kept).  iter_ms (may be NULL) receives a cost
- * model's estimate of one FCF iteration: per level 2m batched steps of N_l/m
- * columns, the FAS step of the next level, the coarsest level's N_L single
- * steps, all at measured step times.  Linear meshes only (MG_EINVAL otherwise). */
+ * others).  iter_ms (may be NULL) receives the chosen hierarchy's measured time per
+ * iteration.  Allocates a trajectory of (N+1) x n doubles; synchronises.  Linear
+ * meshes only (MG_EINVAL otherwise). */
 mg_status mg_plan_levels(mg_ctx* ctx, int fine_level, int coarse_level, int64_t N, double T, int max_levels,
                          mg_opts* opts, double* iter_ms);
 

@@ -279,6 +279,11 @@ GraphPlan* graph_plan_pc(mg_ctx* c, const StepOp& op, int ntile, const mg_solver
 double* graph_plan_solution(GraphPlan* p);
 void graph_plan_run(mg_ctx* c, GraphPlan* p, int k, const mg_solver_opts& so);
 
+// ---- the coarsening planner's probe (mgrit.cu): `iters` MGRIT iterations from
+// a0 = 0 with opts (tolerance ignored); residual history and solve seconds
+void mgrit_probe(mg_ctx* c, int64_t N, double T, const mg_opts& opts, int iters, std::vector<double>& hist,
+                 double& seconds);
+
 // ---- Newton steps for meshes with nonlinear materials (newton.cu)
 bool mesh_is_nonlinear(const mg_ctx* c, int mesh);
 void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opts& so,

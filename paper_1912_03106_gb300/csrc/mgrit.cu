@@ -771,6 +771,27 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
 
 }  // namespace
 
+// A few MGRIT iterations with the given options from a0 = 0 (library-owned
+// trajectory buffer), for the coarsening planner: the residual history and the
+// seconds the iterations took (set-up excluded).
+void mgrit_probe(mg_ctx* c, int64_t N, double T, const mg_opts& opts, int iters, std::vector<double>& hist,
+                 double& seconds) {
+    mg_opts o = opts;
+    o.max_iter = iters;
+    o.tol = 0.0;
+    o.tol_relative = 0;
+    const int64_t n = c->meshes[o.space_level[0]].n;
+    c->host_in.ensure(n * sizeof(double));
+    c->host_out.ensure((size_t)(N + 1) * n * sizeof(double));
+    MG_CUDA(cudaMemsetAsync(c->host_in.p, 0, n * sizeof(double), c->stream));
+    mg_stats st;
+    const mg_status rc = solve_impl(c, N, T, c->host_in.as<double>(), c->host_out.as<double>(), &o, &st);
+    if (rc != MG_OK && rc != MG_EMGRIT_MAXIT && rc != MG_ESTALLED) mg_fail(rc, "mgrit_probe: " + c->err);
+    c->err.clear();
+    hist.assign(st.res_hist, st.res_hist + st.n_hist);
+    seconds = st.t_solve;
+}
+
 extern mg_status mg_guarded_call(mg_ctx* c, void (*fn)(void*), void* arg);
 
 template <class F>

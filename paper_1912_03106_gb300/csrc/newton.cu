@@ -159,7 +159,8 @@ struct Elems {
 };
 
 // MODE 0: y_v = nu |T| G_v . g (the element's part of K(a) a) for the columns in
-// state `want`; MODE 1: N = |T| (nu I + 2 nu' g g^T) for every column.
+// state `want`; MODE 1: N = |T| (nu I + 2 nu' g g^T) for the columns in state SOLVE
+// (the others need no new Jacobian; their Jacobian buffers keep older, finite values).
 // Output ((t * 3 + v) * ne + e) * G + lane.
 template <int MODE>
 __global__ void __launch_bounds__(NTB) kn_elem(Elems E, const double* __restrict__ a, const int* __restrict__ state,
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(NTB) kn_elem(Elems E, const double* __restrict
     const int lc = threadIdx.x % G, gc = t * G + lc;
     const int64_t e = (int64_t)blockIdx.x * (NTB / G) + threadIdx.x / G;
     if (e >= E.ne) return;
-    if (MODE == 0 && state[gc] != want) return;
+    if (state[gc] != (MODE == 0 ? want : (int)ST_SOLVE)) return;
     const int id = __ldg(E.eid + e);
     const double* gr = E.grad + 6 * (int64_t)id;
     double gx = 0.0, gy = 0.0, Gx[3], Gy[3];
@@ -257,16 +258,16 @@ __global__ void kn_first_norm(Cols C, const double* part_g, const double* part_p
     }
 }
 
-// Jacobian on the ELL pattern: J = M/dt + Kc + sum_contrib w . N_e  (every column)
+// Jacobian on the ELL pattern: J = M/dt + Kc + sum_contrib w . N_e (columns in state SOLVE)
 __global__ void __launch_bounds__(NTB) kn_jac(int64_t nW, int64_t ne, const double* __restrict__ M64,
                                               const double* __restrict__ Kc, double inv_dt,
                                               const int32_t* __restrict__ jc_ptr, const int32_t* __restrict__ jc_e,
                                               const double* __restrict__ jc_w, const double* __restrict__ N,
-                                              double* J64, float* J32) {
+                                              double* J64, float* J32, const int* __restrict__ state) {
     const int t = blockIdx.y;
     const int lc = threadIdx.x % G;
     const int64_t q = (int64_t)blockIdx.x * (NTB / G) + threadIdx.x / G;
-    if (q >= nW) return;
+    if (q >= nW || state[t * G + lc] != ST_SOLVE) return;
     double v = __ldg(M64 + q) * inv_dt + __ldg(Kc + q);
     const size_t vs = (size_t)ne * G;
     for (int32_t s = __ldg(jc_ptr + q); s < __ldg(jc_ptr + q + 1); ++s) {
@@ -282,11 +283,12 @@ __global__ void __launch_bounds__(NTB) kn_jac(int64_t nW, int64_t ne, const doub
 // coarse operator: Jc = P^T J P per column through the static Galerkin map
 __global__ void __launch_bounds__(NTB) kn_galerkin(int64_t nWc, int64_t nWf, const int32_t* __restrict__ gptr,
                                                    const int32_t* __restrict__ gsrc, const double* __restrict__ gw,
-                                                   const double* Jf, double* Jc, float* Jc32) {
+                                                   const double* Jf, double* Jc, float* Jc32,
+                                                   const int* __restrict__ state) {
     const int t = blockIdx.y;
     const int lc = threadIdx.x % G;
     const int64_t q = (int64_t)blockIdx.x * (NTB / G) + threadIdx.x / G;
-    if (q >= nWc) return;
+    if (q >= nWc || state[t * G + lc] != ST_SOLVE) return;
     double v = 0.0;
     const double* jf = Jf + (size_t)t * nWf * G + lc;
     for (int32_t s = __ldg(gptr + q); s < __ldg(gptr + q + 1); ++s) v += __ldg(gw + s) * jf[(size_t)__ldg(gsrc + s) * G];
@@ -299,13 +301,15 @@ __global__ void __launch_bounds__(NTB) kn_galerkin(int64_t nWc, int64_t nWf, con
 // Gershgorin ratio sum_j |J_ij| / J_ii (rounded up to float; positive floats order
 // like their bits, so the maximum is an unsigned atomicMax, one per block)
 __global__ void __launch_bounds__(NTB) kn_dinv(int n, int W, int nrb, const int32_t* __restrict__ col,
-                                               const double* J64, float* dinv32, int* flag, unsigned* lam) {
+                                               const double* J64, float* dinv32, int* flag, unsigned* lam,
+                                               const int* __restrict__ state) {
     const int t = blockIdx.x / nrb, rb = blockIdx.x % nrb;
     const int lc = threadIdx.x % G;
     const int i1 = min(n, (rb + 1) * RBS);
     const double* jt = J64 + (size_t)t * W * n * G + lc;
     unsigned gmax = 0u;
-    for (int i = rb * RBS + threadIdx.x / G; i < i1; i += NTB / G) {
+    const bool on = state[t * G + lc] == ST_SOLVE;  // the bound covers the Jacobians in use
+    for (int i = rb * RBS + threadIdx.x / G; on && i < i1; i += NTB / G) {
         double d = 0.0, a = 0.0;
         for (int w = 0; w < W; ++w) {
             const double v = jt[((size_t)w * n + i) * G];
@@ -332,11 +336,11 @@ __global__ void __launch_bounds__(NTB) kn_dinv(int n, int W, int nrb, const int3
 
 // LD32 = J32 . diag(1/d) of the neighbour row, per column
 __global__ void __launch_bounds__(NTB) kn_ld(int64_t nW, int n, const int32_t* __restrict__ col, const float* J32,
-                                             const float* dinv32, float* LD32) {
+                                             const float* dinv32, float* LD32, const int* __restrict__ state) {
     const int t = blockIdx.y;
     const int lc = threadIdx.x % G;
     const int64_t q = (int64_t)blockIdx.x * (NTB / G) + threadIdx.x / G;
-    if (q >= nW) return;
+    if (q >= nW || state[t * G + lc] != ST_SOLVE) return;
     const int j = __ldg(col + q);
     const size_t o = ((size_t)t * nW + q) * G + lc;
     LD32[o] = J32[o] * dinv32[((size_t)t * n + j) * G + lc];
@@ -349,9 +353,11 @@ __global__ void __launch_bounds__(NTB) kn_ld(int64_t nW, int n, const int32_t* _
 // 1/L[i][i] at k = 0 and L[i+k][i] at k = 1..u (entries beyond the matrix are
 // never read).
 __global__ void __launch_bounds__(32) kn_band_factor(int n, int W, int u, int stride, const int32_t* __restrict__ col,
-                                                     const double* J64, float* Lb, float* Ub, int* flag) {
+                                                     const double* J64, float* Lb, float* Ub, int* flag,
+                                                     const int* __restrict__ state) {
     extern __shared__ double win[];
     const int gc = blockIdx.x, t = gc / G, l = gc % G, lane = threadIdx.x;
+    if (state[gc] != ST_SOLVE) return;  // no new Jacobian for this column
     const int U1 = u + 1;
     const double* jt = J64 + (size_t)t * W * n * G + l;
     float* lb = Lb + (size_t)gc * n * stride;
@@ -880,7 +886,7 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
         kn_jac<<<dim3(nblk(nW0, NTB / G), ntile), NTB, 0, s>>>(nW0, N0.ne, d0.M64.as<double>(), N0.Kc.as<double>(),
                                                                1.0 / op.dt, N0.jc_ptr.as<int32_t>(),
                                                                N0.jc_e.as<int32_t>(), N0.jc_w.as<double>(), P->yN,
-                                                               P->J64[0], P->pco.d[0].J32);
+                                                               P->J64[0], P->pco.d[0].J32, P->cols.state);
         launches += 2;
         MG_CUDA(cudaMemsetAsync(P->lam, 0, MG_MAX_DEPTH * sizeof(unsigned), s));
         for (int d = 0; d < nd; ++d) {
@@ -891,15 +897,15 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
                 NlMesh& Nf = nl_mesh(c, P->mesh_of_depth[d - 1]);
                 kn_galerkin<<<dim3(nblk(nW, NTB / G), ntile), NTB, 0, s>>>(
                     nW, (int64_t)mf.ell_W * mf.n, Nf.gal_ptr.as<int32_t>(), Nf.gal_src.as<int32_t>(),
-                    Nf.gal_w.as<double>(), P->J64[d - 1], P->J64[d], P->pco.d[d].J32);
+                    Nf.gal_w.as<double>(), P->J64[d - 1], P->J64[d], P->pco.d[d].J32, P->cols.state);
                 launches += 1;
             }
             const int nrb = (int)((md.n + RBS - 1) / RBS);
             kn_dinv<<<ntile * nrb, NTB, 0, s>>>((int)md.n, md.ell_W, nrb, md.ell_col.as<int32_t>(), P->J64[d],
-                                                P->pco.d[d].dinv32, c->flag.as<int>(), P->lam + d);
+                                                P->pco.d[d].dinv32, c->flag.as<int>(), P->lam + d, P->cols.state);
             kn_ld<<<dim3(nblk(nW, NTB / G), ntile), NTB, 0, s>>>(nW, (int)md.n, md.ell_col.as<int32_t>(),
                                                                  P->pco.d[d].J32, P->pco.d[d].dinv32,
-                                                                 P->pco.d[d].LD32);
+                                                                 P->pco.d[d].LD32, P->cols.state);
             launches += 2;
         }
         {
@@ -911,7 +917,7 @@ void phi_batch_newton(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_sol
             kn_band_factor<<<kpad, 32, smem, s>>>((int)mb.n, mb.ell_W, u, P->pco.band_stride,
                                                   mb.ell_col.as<int32_t>(), P->J64[nd - 1],
                                                   const_cast<float*>(P->pco.band_L), const_cast<float*>(P->pco.band_U),
-                                                  c->flag.as<int>());
+                                                  c->flag.as<int>(), P->cols.state);
             launches += 1;
         }
         // Newton correction of the columns in state SOLVE

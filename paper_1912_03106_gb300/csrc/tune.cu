@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <limits>
@@ -259,29 +260,60 @@ extern "C" mg_status mg_plan_levels(mg_ctx* c, int fine_level, int coarse_level,
             if (mg_choose_levels(ks.data(), ms.data(), (int)ks.size(), A.N, std::max(2, A.max_levels), &levels, m) !=
                 MG_OK)
                 mg_fail(MG_EINVAL, "mg_plan_levels: N has no power-of-two coarsening");
-            // cost model of one FCF iteration: per level (2m-1) relaxation batches + the residual
-            // batch of N_l/m columns, the FAS step of the next level, the coarsest level sequential
-            double est = 0.0;
-            int64_t Nl = A.N;
-            for (int l = 0; l < levels; ++l) {
-                const int mesh = l == 0 ? A.fine : A.coarse;
-                if (l == levels - 1) {
-                    est += (double)Nl * time_step(mesh, Nl, 1);
-                    break;
+            // candidate hierarchies: the heuristic's and fixed factors that divide N; each
+            // runs a few MGRIT iterations, and the one with the least predicted time to
+            // the tolerance is chosen (measured time per iteration x iterations predicted
+            // from the measured residual reduction per iteration)
+            std::vector<std::vector<int>> cands;
+            cands.push_back(std::vector<int>(m, m + levels - 1));
+            for (auto f : std::vector<std::vector<int>>{{16}, {16, 16}, {32, 16}, {8, 8, 8}}) {
+                int64_t prod = 1;
+                for (int v : f) prod *= v;
+                if ((int)f.size() + 1 <= std::max(2, A.max_levels) && A.N % prod == 0 && A.N / prod >= 2 &&
+                    f != cands[0])
+                    cands.push_back(f);
+            }
+            const int probe_iters = 4;
+            const double tol = A.opts->tol > 0.0 ? A.opts->tol : 1e-10;
+            double best_t = std::numeric_limits<double>::infinity(), best_it_ms = 0.0;
+            std::vector<int> best_m = cands[0];
+            for (const auto& f : cands) {
+                mg_opts o = *A.opts;
+                o.levels = (int)f.size() + 1;
+                for (int l = 0; l < 8; ++l) {
+                    o.m[l] = l < (int)f.size() ? f[l] : 0;
+                    o.space_level[l] = l == 0 ? A.fine : A.coarse;
                 }
-                const int k = (int)(Nl / m[l]);
-                const double tk = time_step(mesh, Nl, k);
-                est += (double)(2 * m[l]) * tk;
-                if (l + 1 < levels) est += time_step(A.coarse, Nl / m[l], (int)(Nl / m[l]));
-                Nl /= m[l];
+                std::vector<double> hist;
+                double secs = 0.0;
+                mgrit_probe(c, A.N, A.T, o, probe_iters, hist, secs);
+                const double it_ms = 1e3 * secs / (double)std::max<size_t>(1, hist.size());
+                // reduction per iteration after the first (the first carries the start-up transient)
+                double rho = 1.0;
+                if (hist.size() >= 3 && hist[1] > 0.0) {
+                    const double last = hist.back();
+                    rho = last > 0.0 ? std::pow(last / hist[1], 1.0 / (double)(hist.size() - 2)) : 0.0;
+                }
+                double iters = std::numeric_limits<double>::infinity();
+                if (rho == rho && rho <= 0.0) iters = (double)hist.size();
+                else if (rho == rho && rho < 1.0) iters = 1.0 + std::ceil(std::log(tol) / std::log(rho));
+                const double t = iters * it_ms;
+                if (mg_trace_level() >= 1)
+                    std::fprintf(stderr, "[plan] levels %d m %d %d %d: %.3f ms/iteration, reduction %.3f, %.0f iterations\n",
+                                 o.levels, o.m[0], o.m[1], o.m[2], it_ms, rho, iters);
+                if (t < best_t) {
+                    best_t = t;
+                    best_it_ms = it_ms;
+                    best_m = f;
+                }
             }
             ctx_drop_plans(c);
-            A.opts->levels = levels;
+            A.opts->levels = (int)best_m.size() + 1;
             for (int l = 0; l < 8; ++l) {
-                A.opts->m[l] = l < levels - 1 ? m[l] : 0;
+                A.opts->m[l] = l < (int)best_m.size() ? best_m[l] : 0;
                 A.opts->space_level[l] = l == 0 ? A.fine : A.coarse;
             }
-            if (A.iter_ms) *A.iter_ms = est;
+            if (A.iter_ms) *A.iter_ms = best_it_ms;
         },
         &a);
 }

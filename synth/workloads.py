@@ -6,7 +6,8 @@ level one red refinement (4,512 / 18,240 / 73,344 interior DOFs).
   cfg0_linear_l0_N256      l0, T = 5 ms,  N = 256,   5 kHz carrier, 2-level m=16 F-relax
   cfg1_linear_l2_N4096     l2, T = 20 ms, N = 4096,  20 kHz carrier, 3-level m=16 FCF,
                            coarse time levels on the l0 mesh (direct spatial coarsening)
-  cfg2_mixed_l3_N16384     l3, T = 20 ms, N = 16384, 20 kHz, 3-level m=16 FCF, coarse on l0
+  cfg2_mixed_l3_N16384     l3, T = 20 ms, N = 16384, 20 kHz, 3-level m=16 FCF, delayed spatial
+                           coarsening: level 1 on l3, the coarsest level on l2
   cfg3_nonlinear_l2_N8192  l2 + Brauer law, J0 = 3e6, N = 8192, T = 20 ms, 3-level m=16 FCF
 """
 
@@ -37,7 +38,7 @@ class Workload:
 WORKLOADS = {
     "cfg0_linear_l0_N256": Workload("cfg0_linear_l0_N256", 0, (0, 0), 256, 5.0e-3, (16,), 0, 5.0e3),
     "cfg1_linear_l2_N4096": Workload("cfg1_linear_l2_N4096", 2, (2, 0, 0), 4096, 20.0e-3, (16, 16), 1, 20.0e3),
-    "cfg2_mixed_l3_N16384": Workload("cfg2_mixed_l3_N16384", 3, (3, 0, 0), 16384, 20.0e-3, (16, 16), 1, 20.0e3,
+    "cfg2_mixed_l3_N16384": Workload("cfg2_mixed_l3_N16384", 3, (3, 3, 2), 16384, 20.0e-3, (16, 16), 1, 20.0e3,
                                      precision=1),
     "cfg3_nonlinear_l2_N8192": Workload("cfg3_nonlinear_l2_N8192", 2, (2, 0, 0), 8192, 20.0e-3, (16, 16), 1, 20.0e3,
                                         J0=3.0e6, nonlinear=True),

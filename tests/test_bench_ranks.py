@@ -72,7 +72,8 @@ def test_both_arms_share_the_workload_keys():
     sys.path.insert(0, ROOT)
     import bench
 
-    cfg = bench.workload_config(18240, 1104, 2)
+    cfg = bench.workload_config([1104, 4512, 18240], 2)
     assert cfg["workload"] == bench.WORKLOAD and cfg["space_levels"] == [18240, 1104, 1104]
+    assert bench.workload_config([1104, 4512, 18240, 73344], 1, "cfg2")["space_levels"] == [73344, 73344, 18240]
     assert cfg["parallelism"] == "replicas x2" and cfg["N"] == bench.N_STEPS
     json.dumps(cfg)

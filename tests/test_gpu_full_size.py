@@ -4,7 +4,8 @@ and bench.py use, on outputs the oracle can compute one by one.
 cfg1: 18,240 DOFs, N = 4,096, 3-level FCF MGRIT with coarse levels on the 1,104-DOF
 mesh (the bench's solve), and its level-0 batched step of 256 columns.
 cfg2: 73,344 DOFs, N = 16,384, FP32+refinement: the level-0 batched step of 1,024
-columns, and a 256-step prefix of the time grid through 3-level MGRIT.
+columns, and a 256-step prefix of the time grid through 3-level MGRIT with the
+workload's delayed spatial coarsening.
 cfg3: 18,240 DOFs with the Brauer law, N = 8,192: the level-0 batched Newton step
 of 512 columns.
 Sampled columns / time points are compared with the oracle (banded Cholesky /
@@ -111,7 +112,8 @@ def test_cfg2_level0_step_1024_columns_mixed(meshes):
 
 def test_cfg2_prefix_mgrit_mixed(meshes):
     """The first 256 steps of the cfg2 time grid (dt = 20 ms / 16,384) through
-    3-level FCF MGRIT (m = 16, coarse levels on the 1,104-DOF mesh) in the
+    3-level FCF MGRIT (m = 16, the workload's delayed spatial coarsening: level 1 on
+    the 73,344-DOF mesh, the coarsest level on the 18,240-DOF mesh) in the
     FP32+refinement form: every time point within 1e-6 of the oracle."""
     w = workload("cfg2_mixed_l3_N16384")
     model = machine_model(pwm=PwmSpec(J0=w.J0, f_carrier=w.f_carrier))
@@ -120,8 +122,8 @@ def test_cfg2_prefix_mgrit_mixed(meshes):
     Tp = w.T * Np / w.N
     n = ctx.mg_num_dofs(ids[3])
     out = torch.empty((Np + 1, n), dtype=torch.float64, device="cuda")
-    opts = api.mgrit_opts(levels=3, m=(16, 16), space_level=(ids[3], ids[0], ids[0]), relax=1, tol=1e-6,
-                          max_iter=100, solver=api.solver_opts(precision=1))
+    opts = api.mgrit_opts(levels=3, m=(16, 16), space_level=tuple(ids[s] for s in w.space_levels), relax=1,
+                          tol=1e-6, max_iter=100, solver=api.solver_opts(precision=1))
     rc, st = ctx.mg_solve(Np, Tp, torch.zeros(n, dtype=torch.float64, device="cuda"), out, opts, allow=(-7,))
     assert rc == 0, " ".join("%.2e" % h for h in st["res_hist"])
     fe = fem.FEModel(meshes[3], model)

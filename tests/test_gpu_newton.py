@@ -179,6 +179,37 @@ def test_nonlinear_mgrit_matches_oracle_iterates(meshes, nl):
     assert st["newton_iters"] > 0
 
 
+def test_nonlinear_mgrit_with_spatial_coarsening_follows_oracle(meshes, nl):
+    """Two-level FAS-MGRIT, FCF, with spatial coarsening (Sec. 2.2) under the
+    Brauer law: fine level on the 4,512-DOF mesh, coarse level on the 1,104-DOF
+    mesh (the coarse Newton steps evaluate the law on the coarse mesh).  The
+    iterates after one and two iterations are the oracle's (the residual history
+    too), and the iteration converges to the oracle's sequential Newton stepping."""
+    model, ctx, ids = nl
+    Nm, m = 16, 4
+    Tm = Nm * T / N
+    P = MachineProblem(meshes[:2], model, Nm, Tm, (1, 0), (m,), nonlinear=True)
+    seq = MachineProblem(meshes[:2], model, Nm, Tm, (1,), (), nonlinear=True).sequential()
+    n = seq.shape[1]
+    a0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for iters in (1, 2):
+        u_cpu, hist = P.mgrit(gamma=1, tol=0.0, max_iter=iters, tol_relative=False)
+        out = torch.zeros((Nm + 1, n), dtype=torch.float64, device="cuda")
+        opts = api.mgrit_opts(levels=2, m=(m,), space_level=(ids[1], ids[0]), relax=1, tol=0.0,
+                              tol_relative=False, max_iter=iters)
+        rc, st = ctx.mg_solve(Nm, Tm, a0, out, opts, allow=(-7,))
+        scale = np.linalg.norm(u_cpu[1:], axis=1).max()
+        err = np.linalg.norm(out.cpu().numpy() - u_cpu, axis=1).max() / scale
+        assert err <= 1e-9, (iters, err)
+        h_gpu, h_cpu = np.array(st["res_hist"]), np.array(hist)
+        assert np.all(np.abs(h_gpu - h_cpu) <= 1e-6 * h_cpu + 1e-9 * h_cpu[0]), (h_gpu, h_cpu)
+    out = torch.zeros((Nm + 1, n), dtype=torch.float64, device="cuda")
+    opts = api.mgrit_opts(levels=2, m=(m,), space_level=(ids[1], ids[0]), relax=1, tol=1e-9, max_iter=40)
+    rc, st = ctx.mg_solve(Nm, Tm, a0, out, opts, allow=(-7,))
+    assert rc == 0, st["res_hist"]
+    assert rel_err_per_point(out.cpu().numpy(), seq).max() <= 1e-8
+
+
 def test_static_step_rejects_nonlinear_mesh(meshes, nl):
     model, ctx, ids = nl
     n = ctx.mg_num_dofs(ids[0])
