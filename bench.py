@@ -81,16 +81,20 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "graph_step_l2x256_fp64.md")
 
 
+# the sources of the batched-step graph (its kernels, their device helpers and the
+# shared definitions): the roofline launch's DRAM counters are valid only for them
+STEP_SOURCES = ("batch.cu", "internal.h", "vec.cuh")
+
+
 def csrc_sha1() -> str:
-    """Hash of the library sources: DRAM counters are valid only for the kernels they measured."""
+    """Hash of the batched step's sources: DRAM counters are valid only for the kernels they measured."""
     import hashlib
 
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1912_03106_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in STEP_SOURCES:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()
 
 
@@ -123,6 +127,10 @@ def parse():
     ap.add_argument("--path", type=int, default=0, help="with --profile-step: 0 auto, 1 cluster, 2 graph")
     ap.add_argument("--reps", type=int, default=2, help="with --profile-step: number of steps")
     ap.add_argument("--level", type=int, default=2, help="with --profile-step: mesh level 0..3 (18,240 DOFs = 2)")
+    ap.add_argument("--halo-fusion", type=int, default=0,
+                    help="with --profile-step: halo-fused multigrid kernels (0 library choice, 1 off, 2 on)")
+    ap.add_argument("--base-cores", type=int, default=0,
+                    help="with --profile-step: dense base solve on CUDA (1) or tensor (2) cores, 0 library choice")
     ap.add_argument("--tol", type=float, default=0.0,
                     help="with --profile-step: step tolerance (cg_tol and refine_tol; 0: library default)")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default launch shapes")
@@ -134,6 +142,8 @@ def parse():
                     help="leading time points checked against the CPU oracle (-1: the workload's default)")
     ap.add_argument("--no-sc", action="store_true",
                     help="every MGRIT level on the fine mesh (no spatial coarsening)")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end solves through host buffers (each nonlinear solve takes minutes)")
     return ap.parse_args()
 
 
@@ -164,7 +174,8 @@ def profile_step(args):
                             machine_model(pwm=PwmSpec(J0=1e6, f_carrier=F_CARRIER)))
     k = args.profile_step
     x_in, out = step_inputs(ctx, ids, k, args.level)
-    so = api.solver_opts(precision=args.precision, path=args.path)
+    so = api.solver_opts(precision=args.precision, path=args.path, halo_fusion=args.halo_fusion,
+                         base_cores=args.base_cores)
     if args.tol > 0.0:
         so.cg_tol = so.refine_tol = args.tol
 
@@ -202,13 +213,21 @@ def instances_run(args):
     1,104-DOF ones with the Brauer law), each a 3-level FCF MGRIT solve (m = 16
     on its own mesh, relative tolerance 1e-7 with inexact step solves; linear
     instances in the FP32+refinement form, Brauer-law instances with FP64 Newton
-    steps), solved concurrently by mg_batch_solve and one by one; aggregate
-    step-solves per second of both."""
+    steps).  All instances are solved by one mg_batch_solve under a work budget of
+    the free device memory (their outputs, 101 GB for 64 instances, are allocated
+    first); one by one, each alone with its work buffers freed afterwards, is timed
+    on one instance of every (mesh, N, law) class and scaled by the class sizes.
+    Aggregate step-solves per second of both; two small linear instances are
+    compared with the CPU oracle's sequential stepping at every time point."""
+    import collections
+
+    import numpy as np
     import torch
 
     import synth
     from synth.model import PwmSpec, machine_model
     from synth.workloads import instances
+    from oracle.problem import MachineProblem, rel_err_per_point
     from paper_1912_03106_gb300 import api
 
     meshes = synth.mesh_hierarchy(4)
@@ -227,25 +246,58 @@ def instances_run(args):
         setups.append((ctx, opts, torch.zeros(n, dtype=torch.float64, device="cuda"),
                        torch.zeros((inst.N + 1, n), dtype=torch.float64, device="cuda")))
     torch.cuda.synchronize()
-    args_b = ([s_[0] for s_ in setups], [i.N for i in insts], [i.T for i in insts], [s_[2] for s_ in setups],
-              [s_[3] for s_ in setups], [s_[1] for s_ in setups])
-    api.mg_batch_solve(*args_b)  # warm-up: plans, step operators, PWM tables
+    ctxs, a0s, outs, optss = [s_[0] for s_ in setups], [s_[2] for s_ in setups], [s_[3] for s_ in setups], \
+        [s_[1] for s_ in setups]
+    Ns, Ts = [i.N for i in insts], [i.T for i in insts]
+    # warm-up: step operators and PWM tables (one relaxation each; work buffers freed)
+    warm = []
+    for o in optss:
+        w_ = api.L.mg_opts.from_buffer_copy(o)
+        w_.max_iter = 0
+        warm.append(w_)
+    api.mg_batch_solve(ctxs, Ns, Ts, a0s, outs, warm, work_budget=-1)
+    free_gb = torch.cuda.mem_get_info()[0] / 1e9
     t0 = time.perf_counter()
-    rc, status, stats = api.mg_batch_solve(*args_b)
+    rc, status, stats = api.mg_batch_solve(ctxs, Ns, Ts, a0s, outs, optss, work_budget=-1)
     t_conc = time.perf_counter() - t0
     solves = sum(s_["step_solves"] for s_ in stats)
-    t0 = time.perf_counter()
-    for (ctx, opts, a0, out), inst in zip(setups, insts):
-        ctx.mg_solve(inst.N, inst.T, a0, out, opts, allow=(-7, -10))
-        torch.cuda.current_stream().wait_stream(ctx.stream)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
+    print(json.dumps({"phase": "concurrent", "status": rc, "statuses": sorted(set(status)), "step_solves": solves,
+                      "concurrent_s": t_conc, "concurrent_step_solves_per_s": solves / t_conc,
+                      "iters": [s_["iters"] for s_ in stats]}), file=sys.stderr, flush=True)
+    # oracle: two small linear instances at every time point
+    checks = []
+    for idx in [i for i, inst in enumerate(insts) if not inst.nonlinear and inst.mesh_level <= 1 and
+                inst.N == 1024][:2]:
+        inst = insts[idx]
+        model = machine_model(pwm=PwmSpec(J0=inst.J0, f_carrier=inst.f_carrier))
+        ref = MachineProblem(meshes[:inst.mesh_level + 1], model, inst.N, inst.T, (inst.mesh_level,), ()).sequential()
+        checks.append({"instance": idx, "dofs": int(a0s[idx].numel()), "N": inst.N,
+                       "max_rel_err": float(rel_err_per_point(outs[idx].cpu().numpy(), ref).max())})
+    # one by one: one instance per class, alone, scaled by the class sizes
+    classes = collections.OrderedDict()
+    for i, inst in enumerate(insts):
+        classes.setdefault((int(a0s[i].numel()), inst.N, inst.nonlinear), []).append(i)
+    t_seq, per_class = 0.0, []
+    for (n, N_, nl), members in classes.items():
+        i = members[0]
+        ctx = ctxs[i]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r, st = ctx.mg_solve(Ns[i], Ts[i], a0s[i], outs[i], optss[i], allow=(-7, -10))
+        torch.cuda.synchronize()
+        dt_ = time.perf_counter() - t0
+        ctx.mg_release_work()
+        t_seq += dt_ * len(members)
+        per_class.append({"dofs": n, "N": N_, "nonlinear": nl, "count": len(members), "alone_s": round(dt_, 3),
+                          "step_solves": st["step_solves"], "status": r})
+        print(json.dumps({"phase": "alone", **per_class[-1]}), file=sys.stderr, flush=True)
     print(json.dumps({"instances": len(insts), "status": rc, "statuses": sorted(set(status)),
-                      "mix": {"dofs": [s_[2].numel() for s_ in setups], "N": [i.N for i in insts],
-                              "nonlinear": [i.nonlinear for i in insts]},
+                      "work_budget_gb": round(0.95 * free_gb, 1), "outputs_gb": round(
+                          sum(o.numel() for o in outs) * 8 / 1e9, 1),
                       "step_solves": solves, "concurrent_s": t_conc, "one_by_one_s": t_seq,
+                      "one_by_one": "each class timed alone once, scaled by its size", "classes": per_class,
                       "concurrent_step_solves_per_s": solves / t_conc, "one_by_one_step_solves_per_s": solves / t_seq,
-                      "speedup": t_seq / t_conc, "iters": [s_["iters"] for s_ in stats]}))
+                      "speedup": t_seq / t_conc, "iters": [s_["iters"] for s_ in stats], "oracle_check": checks}))
     for s_ in setups:
         s_[0].close()
 
@@ -346,8 +398,10 @@ class ClockSampler:
 def step_bytes_per_column_iteration(ns, W=7, nu=5, base_tile=16, krylov_bytes=8):
     """Algorithmic bytes one column moves per PCG iteration of the batched step kernel.
 
-    ns: rows per multigrid depth (finest first).  Each vector pass counts once
-    (a gathered vector counts as one read), the ELL matrix (4-byte column index +
+    ns: rows per multigrid depth (finest first).  Each vector pass of the V-cycle
+    with one smoothing sweep per launch counts once (two sweeps per launch move
+    fewer: their intermediate residual stays on the SM; a gathered vector counts as
+    one read), the ELL matrix (4-byte column index +
     4-byte value per entry, 8-byte values for the FP64 operator) once per phase
     for the whole launch, not per column, so it is added by the caller.
     """
@@ -445,7 +499,8 @@ def run_ours(args, rank, world, local):
             tuned["%d_DOFs_x%d" % (ctx.mg_num_dofs(ids[lvl]), kk)] = {
                 "path": "graph" if so.path == 2 else "cluster", "tile": so.tile, "cluster": so.cluster,
                 "rows_per_block": so.rows_per_block, "coarse_rows_per_block": so.coarse_rows_per_block,
-                "base_tiles": so.base_tiles, "ms": round(ms, 4)}
+                "base_tiles": so.base_tiles, "halo_fusion": so.halo_fusion, "base_cores": so.base_cores,
+                "ms": round(ms, 4)}
 
     def barrier():
         torch.cuda.synchronize()
@@ -554,19 +609,23 @@ def run_ours(args, rank, world, local):
                "max_rel_err_vs_reference": max_rel_err(out), "step_solves_per_s": st_a["step_solves"] / ta}
 
     # end to end through the host-buffer entry point (pinned host memory)
-    a0_h = torch.zeros(n, dtype=torch.float64).pin_memory()
-    out_h = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
-    a0_np, out_np = a0_h.numpy(), out_h.numpy()
-    if not w.nonlinear:  # warm (a nonlinear solve takes minutes; its plans exist already)
-        ctx.mg_solve_host(N, T, a0_np, out_np, opts)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.mg_solve_host(N, T, a0_np, out_np, opts)
-    barrier()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
-    e2e_err = max_rel_err(torch.as_tensor(out_np).to(dev))
-    del out_h
+    e2e = None
+    if not args.no_e2e:
+        a0_h = torch.zeros(n, dtype=torch.float64).pin_memory()
+        out_h = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
+        a0_np, out_np = a0_h.numpy(), out_h.numpy()
+        if not w.nonlinear:  # warm (a nonlinear solve takes minutes; its plans exist already)
+            ctx.mg_solve_host(N, T, a0_np, out_np, opts)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.mg_solve_host(N, T, a0_np, out_np, opts)
+        barrier()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+        e2e = {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 8,
+               "d2h_bytes_per_step": (N + 1) * n * 8,
+               "max_rel_err_vs_reference": max_rel_err(torch.as_tensor(out_np).to(dev))}
+        del out_h
 
     roof = roofline(ctx, ids, w, stream)
 
@@ -636,8 +695,7 @@ def run_ours(args, rank, world, local):
         "error_reference": ref_note,
         "spatial_coarsening": not args.no_sc,
         "oracle_check": oracle,
-        "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 8,
-                "d2h_bytes_per_step": (N + 1) * n * 8, "max_rel_err_vs_reference": e2e_err},
+        "e2e": e2e,
         "roofline": roof,
         "clocks": clocks.summary(),
         "gpu_launches": int(sum(s_["launches"] for s_ in stats)),

@@ -203,7 +203,19 @@ typedef struct {
     int smoother;              /* mg_smoother                                               */
     double cheb_ratio;         /* MG_SMOOTH_CHEBYSHEV: lam over the lower end of the damped
                                   interval (1 < cheb_ratio <= 1e4), 0 = library choice (30) */
+    int halo_fusion;           /* graph path, linear steps: 2 = kernels that keep an
+                                  intermediate vector in shared memory on a halo of the
+                                  operator's bandwidth (two consecutive smoothing sweeps per
+                                  launch; the prolongation with the residual update), where the
+                                  halo fits; 1 = one kernel per sweep and per transfer;
+                                  0 = library choice (2).  Same arithmetic either way. */
+    int base_cores;            /* graph path, linear steps: the dense base solve x = A^-1 r of
+                                  the V-cycle on MG_BASE_CUDA (FP32 FMA) or MG_BASE_TENSOR
+                                  (3xTF32 mma.sync, FP32-level accuracy) cores, 0 = library
+                                  choice (MG_BASE_CUDA) */
 } mg_solver_opts;
+#define MG_BASE_CUDA 1
+#define MG_BASE_TENSOR 2
 
 /* Fill opts with the library defaults (cg_tol 1e-13, refine_tol 1e-13,
  * inner_tol 3e-2, max_cg 2000, max_refine 30, FP64, multigrid with 5 Chebyshev
@@ -289,10 +301,12 @@ mg_status mg_step_static(mg_ctx* ctx, int level, int64_t N, double T, int64_t dt
  * columns on mesh `level` (dt = T/N; start states are a fixed pseudo-random
  * pattern generated on the device) for a set of launch shapes -- cluster path
  * with tile width 1/8/16 and 8 or 16 CTAs per cluster, or graph path with rows
- * per block on the finest and coarser depths and base-solve tiles per block --
- * by coordinate descent from the library's choice, 3 timed steps per shape.
- * The fastest shape is written into *opts (path, tile, cluster, rows_per_block,
- * coarse_rows_per_block, base_tiles; other fields kept) and recorded in the
+ * per block on the finest and coarser depths, halo-fused multigrid kernels or
+ * not, the cores of the dense base solve and its tiles per block -- by
+ * coordinate descent from the library's choice, 3 timed steps per shape.  The
+ * fastest shape is written into *opts (path, tile, cluster, rows_per_block,
+ * coarse_rows_per_block, halo_fusion, base_cores, base_tiles; other fields
+ * kept) and recorded in the
  * context for (level, k) -- k rounded up to whole 16-column tiles above 16 --,
  * where steps with path MG_PATH_AUTO and a zero shape pick it up (MGRIT
  * relaxation batches included).  best_ms (may
@@ -353,6 +367,18 @@ void mg_opts_defaults(mg_opts* opts);
 mg_status mg_solve(mg_ctx* ctx, int64_t N, double T, const double* a0, double* out,
                    const mg_opts* opts, mg_stats* stats);
 
+/* Estimated device bytes of the work buffers mg_solve(ctx, N, ..., opts) allocates
+ * in the context (its level storage, exactly, and the batched-step plans of its
+ * relaxation batches; the caller's a0 and out not included) into *bytes.  No
+ * device work.  MG_EINVAL for bad options. */
+mg_status mg_solve_work_bytes(mg_ctx* ctx, int64_t N, const mg_opts* opts, int64_t* bytes);
+
+/* Frees the context's work buffers: step plans and their CUDA graphs, the solve
+ * storage, step work vectors and host staging (all re-created on the next call
+ * that needs them).  Meshes, operators, transfers and tuned shapes stay.
+ * Synchronises the context's stream. */
+mg_status mg_release_work(mg_ctx* ctx);
+
 /* Several independent machine instances at once (the paper has no counterpart):
  * instance i is context ctxs[i] (its own meshes, materials, PWM and stream; the
  * contexts must be distinct and should use distinct streams) solved with N[i],
@@ -360,12 +386,21 @@ mg_status mg_solve(mg_ctx* ctx, int64_t N, double T, const double* a0, double* o
  * opts[i], or by mg_sequential on opts[i].space_level[0] with opts[i].solver when
  * opts[i].levels == 1.  Each instance is driven by a host worker thread, at most
  * max_threads at a time (0 = one per instance), so the instances' kernels run
- * concurrently on the GPU.  status[i] and stats[i] (either may be NULL) receive
- * each instance's status and statistics; the call returns the worst status and
- * returns when every instance's stream is idle. */
+ * concurrently on the GPU.
+ * work_budget bounds the device memory of the instances' work buffers (the a0 and
+ * out of every instance are the caller's and not counted): 0 = no bound (every
+ * instance may run at once; work buffers stay allocated afterwards); > 0 = bytes,
+ * -1 = the device's free memory at the call less 5 %.  With a bound, instances
+ * start in order of decreasing mg_solve_work_bytes, each only while the estimates
+ * of the running ones and its own fit the bound (or when none runs), and each
+ * instance's work buffers are released (mg_release_work) when it ends; an instance
+ * that ran out of device memory next to others is solved again alone at the end.
+ * status[i] and stats[i] (either may be NULL) receive each instance's status and
+ * statistics; the call returns the worst status and returns when every instance's
+ * stream is idle. */
 mg_status mg_batch_solve(mg_ctx* const* ctxs, int n, const int64_t* N, const double* T,
                          const double* const* a0, double* const* out, const mg_opts* opts,
-                         int max_threads, mg_status* status, mg_stats* stats);
+                         int max_threads, int64_t work_budget, mg_status* status, mg_stats* stats);
 
 /* Joule losses (Eq. losses, per unit depth) of a trajectory on mesh `level`:
  * losses[i] = d_i^T M_sigma d_i with d_i = (traj[i] - traj[i-1]) / (T/N) for

@@ -246,6 +246,16 @@ class Context:
         self._check(rc, allow=allow)
         return rc, stats_dict(st)
 
+    def mg_solve_work_bytes(self, N, opts: L.mg_opts) -> int:
+        """Estimated device bytes of the work buffers mg_solve allocates for N steps."""
+        b = C.c_int64(0)
+        self._check(self.lib.mg_solve_work_bytes(self.h, N, C.byref(opts), C.byref(b)))
+        return b.value
+
+    def mg_release_work(self):
+        """Free the context's work buffers (step plans, solve storage); meshes and operators stay."""
+        self._check(self.lib.mg_release_work(self.h))
+
     def mg_solve_host(self, N, T, a0: np.ndarray, out: np.ndarray, opts: L.mg_opts, allow=()):
         assert a0.dtype == np.float64 and out.dtype == np.float64
         st = L.mg_stats()
@@ -280,11 +290,13 @@ def setup_machine(ctx: Context, meshes, model) -> list:
     return ids
 
 
-def mg_batch_solve(ctxs, N, T, a0, out, opts, max_threads=0):
+def mg_batch_solve(ctxs, N, T, a0, out, opts, max_threads=0, work_budget=0):
     """Solve independent instances concurrently (one Context each, distinct streams).
 
     N, T, a0, out, opts: one entry per instance (a0/out device tensors as for
-    Context.mg_solve).  Returns (worst status, [status], [stats dict]).
+    Context.mg_solve).  work_budget: device bytes the running instances' work
+    buffers may take together (0: no limit, -1: the free device memory; see
+    mg_batch_solve in the header).  Returns (worst status, [status], [stats dict]).
     """
     n = len(ctxs)
     lib = L.load()
@@ -299,7 +311,7 @@ def mg_batch_solve(ctxs, N, T, a0, out, opts, max_threads=0):
     op = (L.mg_opts * n)(*opts)
     st = (C.c_int * n)()
     stats = (L.mg_stats * n)()
-    rc = lib.mg_batch_solve(hs, n, Ns, Ts, a0p, outp, op, max_threads, st, stats)
+    rc = lib.mg_batch_solve(hs, n, Ns, Ts, a0p, outp, op, max_threads, work_budget, st, stats)
     return rc, [L.STATUS.get(v, v) for v in st], [stats_dict(s) for s in stats]
 
 

@@ -106,6 +106,10 @@ struct Depth {
     // per column tile: 0 once all of its columns have stopped iterating; the PCG and
     // multigrid kernels then skip the tile (its vectors and partials stay as they are)
     const int* tact;
+    // two smoothing sweeps per launch (kb_smooth2): columns and rows per block, the
+    // operator's bandwidth max |i - j| and the row blocks per column group; f_cw = 0:
+    // one sweep per launch
+    int f_cw, f_R, f_H, f_nrb;
 };
 
 struct Cols {
@@ -734,6 +738,97 @@ __global__ void __launch_bounds__(NTB, minb_s<PC>()) kb_smooth(Depth D, const fl
     }
 }
 
+// Two consecutive smoothing sweeps in one launch, for operators shared by all
+// columns.  Sweep a: x1 = x0 + wa D^-1 s0, s1 = s0 - wa (L D^-1) s0; sweep b:
+// x2 = x1 + wb D^-1 s1 and, unless dst is null, s2 = s1 - wb (L D^-1) s1.  FIRST:
+// the depth's first sweep, x0 = 0 and s0 the V-cycle's input residual.  A block
+// owns rows [a, a + R) of CW columns of one tile.  It forms s1 in shared memory on
+// every row within the operator's bandwidth H of its own rows, [a - H, a + R + H),
+// reading s0 through L2, so that the second sweep gathers s1 from shared memory and
+// s1 never leaves the SM; the halo rows' first sweep is done by both neighbouring
+// blocks.  Same arithmetic, in the same order, as kb_smooth_first / kb_smooth.
+constexpr int NT2 = 512;
+template <int CW, bool FIRST>
+__global__ void __launch_bounds__(NT2, 2) kb_smooth2(Depth D, const float* s0_base, float* dst_base, float wa,
+                                                     float wb) {
+    extern __shared__ float4 s1sh[];  // (R + 2H) rows x CW floats
+    constexpr int TPR = CW / VF, RPP = NT2 / TPR, NSUB = G / CW;
+    phase_begin();
+    const int rb = blockIdx.x % D.f_nrb;
+    const int grp = blockIdx.x / D.f_nrb;
+    const int t = grp / NSUB;
+    if (!tile_on(D.tact, t)) return;
+    const int l = threadIdx.x % TPR;
+    const int c0 = (grp % NSUB) * CW + l * VF;
+    const int a = rb * D.f_R, b = min(D.n, a + D.f_R);
+    const int lo = max(0, a - D.f_H), hi = min(D.n, b + D.f_H);
+    const float* s0 = tv(s0_base, D.n, t);
+    for (int i = lo + (int)threadIdx.x / TPR; i < hi; i += RPP) {
+        float sv[VF], acc[VF];
+        vld<float, VF>(s0 + i * G + c0, sv);
+        ell_vec_w<VF, float, float, float, false>(D.col, D.LD32, D.n, D.W, i, s0, c0, acc);
+        float4 o;
+        o.x = sv[0] - wa * acc[0];
+        o.y = sv[1] - wa * acc[1];
+        o.z = sv[2] - wa * acc[2];
+        o.w = sv[3] - wa * acc[3];
+        s1sh[(i - lo) * TPR + l] = o;
+    }
+    __syncthreads();
+    float* x = tv(D.x, D.n, t);
+    float* dst = dst_base ? tv(dst_base, D.n, t) : nullptr;
+    for (int i = a + (int)threadIdx.x / TPR; i < b; i += RPP) {
+        const float4 s1v = s1sh[(i - lo) * TPR + l];
+        const float s1[VF] = {s1v.x, s1v.y, s1v.z, s1v.w};
+        float sv[VF], xv[VF];
+        vld<float, VF>(s0 + i * G + c0, sv);
+        const float di = __ldg(D.dinv32 + i);
+        if constexpr (FIRST) {
+#pragma unroll
+            for (int e = 0; e < VF; ++e) xv[e] = wa * di * sv[e];
+        } else {
+            vld<float, VF>(x + i * G + c0, xv);
+#pragma unroll
+            for (int e = 0; e < VF; ++e) xv[e] = xv[e] + wa * di * sv[e];
+        }
+#pragma unroll
+        for (int e = 0; e < VF; ++e) xv[e] = xv[e] + wb * di * s1[e];
+        vst<float, VF>(x + i * G + c0, xv);
+        if (dst) {
+            float acc[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
+            int j[WMAX];
+            float v[WMAX];
+#pragma unroll
+            for (int w = 0; w < WMAX; ++w)
+                if (w < D.W) {
+                    j[w] = __ldg(D.col + w * D.n + i);
+                    v[w] = __ldg(D.LD32 + w * D.n + i);
+                }
+#pragma unroll
+            for (int w = 0; w < WMAX; ++w)
+                if (w < D.W) {
+                    const float4 sj = s1sh[(j[w] - lo) * TPR + l];
+                    acc[0] += v[w] * sj.x;
+                    acc[1] += v[w] * sj.y;
+                    acc[2] += v[w] * sj.z;
+                    acc[3] += v[w] * sj.w;
+                }
+            for (int w = WMAX; w < D.W; ++w) {
+                const float4 sj = s1sh[(__ldg(D.col + w * D.n + i) - lo) * TPR + l];
+                const float vw = __ldg(D.LD32 + w * D.n + i);
+                acc[0] += vw * sj.x;
+                acc[1] += vw * sj.y;
+                acc[2] += vw * sj.z;
+                acc[3] += vw * sj.w;
+            }
+            float so[VF];
+#pragma unroll
+            for (int e = 0; e < VF; ++e) so[e] = s1[e] - wb * acc[e];
+            vst<float, VF>(dst + i * G + c0, so);
+        }
+    }
+}
+
 // r_c = P^T s over the coarse rows (grid over the coarse depth's row blocks)
 __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_restrict(Depth D, Depth C, const float* src_base) {
     phase_begin();
@@ -782,6 +877,91 @@ __global__ void __launch_bounds__(NTB, MG_MINB_F) kb_prolong(Depth D, Depth C, i
         for (int e = 0; e < VF; ++e) xv[e] += yv[e];
         vst<float, VF>(x + i * G + c0, xv);
         vst<float, VF>(tv(D.y, D.n, t) + i * G + c0, yv);
+    }
+}
+
+// Prolongation and residual update in one launch, for operators shared by all
+// columns: y = P x_c, x += y, s -= L y.  A block owns rows [a, a + R) of CW
+// columns of one tile (the kb_smooth2 shape) and forms y in shared memory on the
+// rows within the bandwidth H of them, so y never leaves the SM.  Same arithmetic,
+// in the same order, as kb_prolong followed by kb_resupdate.
+template <int CW>
+__global__ void __launch_bounds__(NT2, 2) kb_prolong_res(Depth D, Depth C, int parts, size_t pstride,
+                                                         float* s_base) {
+    extern __shared__ float4 ysh[];  // (R + 2H) rows x CW floats
+    constexpr int TPR = CW / VF, RPP = NT2 / TPR, NSUB = G / CW;
+    phase_begin();
+    const int rb = blockIdx.x % D.f_nrb;
+    const int grp = blockIdx.x / D.f_nrb;
+    const int t = grp / NSUB;
+    if (!tile_on(D.tact, t)) return;
+    const int l = threadIdx.x % TPR;
+    const int c0 = (grp % NSUB) * CW + l * VF;
+    const int a = rb * D.f_R, b = min(D.n, a + D.f_R);
+    const int lo = max(0, a - D.f_H), hi = min(D.n, b + D.f_H);
+    const float* xc = tv(C.x, C.n, t);
+    for (int i = lo + (int)threadIdx.x / TPR; i < hi; i += RPP) {
+        float yv[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int p = __ldg(D.par + q * D.n + i);
+            if (p >= 0) {
+                const float wq = __ldg(D.pw + q * D.n + i);
+                float xv[VF];
+                vld<float, VF>(xc + p * G + c0, xv);
+                for (int sp = 1; sp < parts; ++sp) {
+                    float xs[VF];
+                    vld<float, VF>(xc + sp * pstride + p * G + c0, xs);
+#pragma unroll
+                    for (int e = 0; e < VF; ++e) xv[e] += xs[e];
+                }
+#pragma unroll
+                for (int e = 0; e < VF; ++e) yv[e] += wq * xv[e];
+            }
+        }
+        ysh[(i - lo) * TPR + l] = make_float4(yv[0], yv[1], yv[2], yv[3]);
+    }
+    __syncthreads();
+    float* x = tv(D.x, D.n, t);
+    float* s = tv(s_base, D.n, t);
+    for (int i = a + (int)threadIdx.x / TPR; i < b; i += RPP) {
+        const float4 yi = ysh[(i - lo) * TPR + l];
+        const float yv[VF] = {yi.x, yi.y, yi.z, yi.w};
+        float xv[VF], sv[VF];
+        vld<float, VF>(x + i * G + c0, xv);
+        vld<float, VF>(s + i * G + c0, sv);
+#pragma unroll
+        for (int e = 0; e < VF; ++e) xv[e] += yv[e];
+        vst<float, VF>(x + i * G + c0, xv);
+        float acc[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
+        int j[WMAX];
+        float v[WMAX];
+#pragma unroll
+        for (int w = 0; w < WMAX; ++w)
+            if (w < D.W) {
+                j[w] = __ldg(D.col + w * D.n + i);
+                v[w] = __ldg(D.L32 + w * D.n + i);
+            }
+#pragma unroll
+        for (int w = 0; w < WMAX; ++w)
+            if (w < D.W) {
+                const float4 yj = ysh[(j[w] - lo) * TPR + l];
+                acc[0] += v[w] * yj.x;
+                acc[1] += v[w] * yj.y;
+                acc[2] += v[w] * yj.z;
+                acc[3] += v[w] * yj.w;
+            }
+        for (int w = WMAX; w < D.W; ++w) {
+            const float4 yj = ysh[(__ldg(D.col + w * D.n + i) - lo) * TPR + l];
+            const float vw = __ldg(D.L32 + w * D.n + i);
+            acc[0] += vw * yj.x;
+            acc[1] += vw * yj.y;
+            acc[2] += vw * yj.z;
+            acc[3] += vw * yj.w;
+        }
+#pragma unroll
+        for (int e = 0; e < VF; ++e) sv[e] -= acc[e];
+        vst<float, VF>(s + i * G + c0, sv);
     }
 }
 
@@ -917,6 +1097,82 @@ __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __rest
     }
 }
 
+// The same contraction on the CUDA cores in FP32 (same block shape, K split and
+// partial outputs as kb_base_dense).  A thread owns 4 rows x CT columns of the
+// block's 64 x TB*16 outputs; the A slice is staged transposed so that a thread
+// reads its 4 rows of one k as one float4, the r slice row-major so that it reads
+// its CT columns as float4s.
+template <class RT, int TB, int BKT>
+__global__ void __launch_bounds__(128) kb_base_cc(int n0, const float* __restrict__ A, const RT* r_base, float* x_base,
+                                                  int ntile, int ks, size_t pstride) {
+    constexpr int NC = TB * G;        // columns per block
+    constexpr int CT = NC / 8;        // columns per thread (8 column groups)
+    phase_begin();
+    __shared__ __align__(16) float At[BKT][64 + 4];
+    __shared__ __align__(16) float Bs[BKT][NC];
+    const int nrb = (n0 + 63) / 64;
+    const int split = blockIdx.x % ks, bt = blockIdx.x / ks;
+    const int cg = bt / nrb, ib = bt % nrb;
+    const int kspan = ((n0 + ks - 1) / ks + BKT - 1) / BKT * BKT;
+    const int kbeg = split * kspan, kend = min(n0, kbeg + kspan);
+    x_base += (size_t)split * pstride;
+    const int r0 = (threadIdx.x / 8) * 4, c0 = (threadIdx.x % 8) * CT;
+    float acc[4][CT] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += BKT) {
+        for (int q = threadIdx.x; q < 64 * BKT; q += 128) {
+            const int rr = q / BKT, kk = q % BKT;
+            const int gi = ib * 64 + rr, gk = k0 + kk;
+            At[kk][rr] = (gi < n0 && gk < kend) ? __ldg(A + (size_t)gi * n0 + gk) : 0.0f;
+        }
+        for (int q = threadIdx.x; q < BKT * NC; q += 128) {
+            const int kk = q / NC, cc = q % NC;
+            const int t = cg * TB + cc / G, gk = k0 + kk;
+            Bs[kk][cc] = (gk < kend && t < ntile) ? (float)r_base[((size_t)t * n0 + gk) * G + cc % G] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < BKT; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(&At[kk][r0]);
+            float b[CT];
+            if constexpr (CT % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < CT; q += 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(&Bs[kk][c0 + q]);
+                    b[q] = v.x;
+                    b[q + 1] = v.y;
+                    b[q + 2] = v.z;
+                    b[q + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < CT; q += 2) {
+                    const float2 v = *reinterpret_cast<const float2*>(&Bs[kk][c0 + q]);
+                    b[q] = v.x;
+                    b[q + 1] = v.y;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                acc[0][c] += a.x * b[c];
+                acc[1][c] += a.y * b[c];
+                acc[2][c] += a.z * b[c];
+                acc[3][c] += a.w * b[c];
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+        const int gi = ib * 64 + r0 + rr;
+        if (gi >= n0) continue;
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            const int cc = c0 + c, t = cg * TB + cc / G;
+            if (t < ntile) x_base[((size_t)t * n0 + gi) * G + cc % G] = acc[rr][c];
+        }
+    }
+}
+
 // launch with the programmatic-dependent-launch attribute (see phase_begin)
 template <typename... KArgs, typename... Args>
 void pdl_launch(void (*kern)(KArgs...), unsigned g, unsigned b, size_t smem, cudaStream_t s, Args... args) {
@@ -943,18 +1199,21 @@ void pdl_launch(void (*kern)(KArgs...), unsigned g, unsigned b, size_t smem, cud
 #endif
 template <class RT>
 void launch_base_dense(cudaStream_t s, int n0, const float* A, const RT* r, float* x, int ntile, int ks,
-                       size_t pstride, int tb) {
+                       size_t pstride, int tb, bool cuda_cores) {
     const int nrb = (n0 + 63) / 64;
     if (tb <= 0) tb = ks > 1 ? MG_BASE_TB : 1;  // library choice
     if (tb >= 4 && ntile >= 4) {
         const unsigned nb = (unsigned)(nrb * ((ntile + 3) / 4) * ks);
-        pdl_launch(kb_base_dense<RT, 4, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
+        if (cuda_cores) pdl_launch(kb_base_cc<RT, 4, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
+        else pdl_launch(kb_base_dense<RT, 4, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
     } else if (tb >= 2 && ntile >= 2) {
         const unsigned nb = (unsigned)(nrb * ((ntile + 1) / 2) * ks);
-        pdl_launch(kb_base_dense<RT, 2, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
+        if (cuda_cores) pdl_launch(kb_base_cc<RT, 2, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
+        else pdl_launch(kb_base_dense<RT, 2, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
     } else {
         const unsigned nb = (unsigned)(nrb * ntile * ks);
-        pdl_launch(kb_base_dense<RT, 1, 128>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
+        if (cuda_cores) pdl_launch(kb_base_cc<RT, 1, 64>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
+        else pdl_launch(kb_base_dense<RT, 1, 128>, nb, 128, 0, s, n0, A, r, x, ntile, ks, pstride);
     }
 }
 
@@ -1232,6 +1491,9 @@ struct GraphPlan {
     int ntile = 0, precision = 0, precond = 1, nu = 2;
     bool pc = false;   // per-column operators (Newton Jacobians), see graph_plan_pc
     int rbs0 = 0, rbs1 = 0, base_tb = 0;  // launch shape (0: library choice)
+    int hf = 0;                            // mg_solver_opts::halo_fusion
+    int bc = 0;                            // mg_solver_opts::base_cores
+    bool base_cc = false;                  // dense base solve on the CUDA cores
     PcOperator pco{};
     float omega = 0.7f;
     int smoother = 0;
@@ -1269,6 +1531,22 @@ void* alloc(GraphPlan& P, size_t bytes) {
 inline unsigned grid(int ntile, int nrb) { return (unsigned)(ntile * nrb); }
 
 
+template <bool FIRST>
+void smooth2_launch(GraphPlan& P, const Depth& D, cudaStream_t s, const float* src, float* dst, float wa, float wb) {
+    const unsigned g = (unsigned)(P.ntile * (G / D.f_cw) * D.f_nrb);
+    const size_t smem = (size_t)(D.f_R + 2 * D.f_H) * D.f_cw * sizeof(float);
+    if (D.f_cw == 8) pdl_launch(kb_smooth2<8, FIRST>, g, NT2, smem, s, D, src, dst, wa, wb);
+    else pdl_launch(kb_smooth2<16, FIRST>, g, NT2, smem, s, D, src, dst, wa, wb);
+}
+
+void prolong_res_launch(GraphPlan& P, const Depth& D, const Depth& C, cudaStream_t s, int parts, size_t pstride,
+                        float* sv) {
+    const unsigned g = (unsigned)(P.ntile * (G / D.f_cw) * D.f_nrb);
+    const size_t smem = (size_t)(D.f_R + 2 * D.f_H) * D.f_cw * sizeof(float);
+    if (D.f_cw == 8) pdl_launch(kb_prolong_res<8>, g, NT2, smem, s, D, C, parts, pstride, sv);
+    else pdl_launch(kb_prolong_res<16>, g, NT2, smem, s, D, C, parts, pstride, sv);
+}
+
 // one preconditioner application on the capture stream: z = B r into depth[0].x;
 // the last kernel writes the (r, z) partials into part.  PC: per-column operators
 // at every depth and a per-column banded Cholesky factor on the base depth.
@@ -1286,12 +1564,26 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
         Depth& D = P.depth[d];
         const float* ws = P.wsm[d];
         const unsigned* lam = P.wlam ? P.pco.lam + d : nullptr;
-        if (d == 0) pdl_launch(kb_smooth_first<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, ws[0], lam);
-        else pdl_launch(kb_smooth_first<float, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.r, ws[0], lam);
+        int sw;
+        if (!PC && std::is_same<RT, float>::value && D.f_cw && P.nu >= 2) {
+            // sweeps 0 and 1 in one launch: x from the residual, s into sa
+            smooth2_launch<true>(P, D, s, d == 0 ? (const float*)rtop : D.r, D.sa, ws[0], ws[1]);
+            sw = 2;
+        } else {
+            if (d == 0) pdl_launch(kb_smooth_first<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, rtop, ws[0], lam);
+            else pdl_launch(kb_smooth_first<float, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, D.r, ws[0], lam);
+            sw = 1;
+        }
         int sl = 0;
-        for (int sw = 1; sw < P.nu; ++sw) {
-            pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa, sl ? D.sa : D.sb, nullptr,
-                       ws[sw], lam, nullptr);
+        while (sw < P.nu) {
+            if (!PC && D.f_cw && sw + 1 < P.nu) {
+                smooth2_launch<false>(P, D, s, sl ? D.sb : D.sa, sl ? D.sa : D.sb, ws[sw], ws[sw + 1]);
+                sw += 2;
+            } else {
+                pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa, sl ? D.sa : D.sb,
+                           nullptr, ws[sw], lam, nullptr);
+                sw += 1;
+            }
             sl ^= 1;
         }
         sel[d] = sl;
@@ -1310,9 +1602,11 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
         else pdl_launch(kb_base_band<float>, nb, 32 * BAND_WARPS, smem, s, B.n, P.pco.band_u, P.pco.band_stride,
                                                                   P.pco.band_L, P.pco.band_U, B.r, B.x);
     } else if (P.op->base_inv.p) {
-        if (nd == 1) launch_base_dense<RT>(s, B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0, P.base_tb);
-        else launch_base_dense<float>(s, B.n, P.op->base_inv.as<float>(), B.r, B.x, P.ntile, ks, pstride,
-                                      P.base_tb);
+        if (nd == 1)
+            launch_base_dense<RT>(s, B.n, P.op->base_inv.as<float>(), rtop, B.x, P.ntile, 1, 0, P.base_tb, P.base_cc);
+        else
+            launch_base_dense<float>(s, B.n, P.op->base_inv.as<float>(), B.r, B.x, P.ntile, ks, pstride, P.base_tb,
+                                     P.base_cc);
         parts = ks;
     } else {
         if (nd == 1) pdl_launch(kb_jacobi<RT, PC>, grid(P.ntile, B.nrb), NTB, 0, s, B, rtop, w, nullptr);
@@ -1329,16 +1623,31 @@ void capture_precondition_t(GraphPlan& P, cudaStream_t s, const RT* rtop, double
         Depth& D = P.depth[d];
         Depth& C = P.depth[d + 1];
         const bool from_base = d + 1 == nd - 1;
-        pdl_launch(kb_prolong, grid(P.ntile, D.nrb), NTB, 0, s, D, C, from_base ? parts : 1, pstride);
         int sl = sel[d];
-        pdl_launch(kb_resupdate<PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa);
-        for (int sw = 0; sw < P.nu; ++sw) {
+        if (!PC && D.f_cw) {
+            prolong_res_launch(P, D, C, s, from_base ? parts : 1, pstride, sl ? D.sb : D.sa);
+        } else {
+            pdl_launch(kb_prolong, grid(P.ntile, D.nrb), NTB, 0, s, D, C, from_base ? parts : 1, pstride);
+            pdl_launch(kb_resupdate<PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa);
+        }
+        for (int sw = 0; sw < P.nu;) {
+            // a pair of sweeps in one launch unless its second sweep is the finest
+            // depth's last, which also accumulates (r, z)
+            const bool pair_last = sw + 1 == P.nu - 1;
+            if (!PC && D.f_cw && sw + 1 < P.nu && !(pair_last && d == 0)) {
+                smooth2_launch<false>(P, D, s, sl ? D.sb : D.sa, pair_last ? nullptr : (sl ? D.sa : D.sb),
+                                      P.wsm[d][P.nu - 1 - sw], P.wsm[d][P.nu - 2 - sw]);
+                sw += 2;
+                sl ^= 1;
+                continue;
+            }
             const bool last = sw == P.nu - 1;
             const bool top = last && d == 0;
             pdl_launch(kb_smooth<RT, PC>, grid(P.ntile, D.nrb), NTB, 0, s, D, sl ? D.sb : D.sa,
                        last ? nullptr : (sl ? D.sa : D.sb), top ? rtop : nullptr, P.wsm[d][P.nu - 1 - sw],
                        P.wlam ? P.pco.lam + d : nullptr, top ? part : nullptr);
             sl ^= 1;
+            ++sw;
         }
     }
 }
@@ -1417,6 +1726,40 @@ cudaGraphConditionalHandle new_handle(cudaStream_t s) {
     return h;
 }
 
+// Launch shape of kb_smooth2 on a depth of n rows with bandwidth H over ntile
+// column tiles: columns (8 or 16) and rows per block such that two blocks of NT2
+// threads fit an SM (shared memory (R + 2H) CW floats each) and the halo is at
+// most 60 % of a block's rows (beyond that two single sweeps are cheaper); among
+// those the one with the least first-sweep work per SM (waves x halo-extended rows
+// x columns).  False if none qualifies.
+constexpr size_t SMOOTH2_SMEM_MAX = 113 * 1024;
+bool smooth2_shape(int n, int H, int ntile, int sms, int& cw, int& R) {
+    double best = 0.0;
+    bool ok = false;
+    for (int c : {8, 16})
+        for (int r : {2048, 1536, 1024, 768, 512, 384, 256}) {
+            if (2.0 * H > 0.6 * r) continue;
+            const size_t smem = (size_t)(r + 2 * H) * c * sizeof(float);
+            if (smem > SMOOTH2_SMEM_MAX) continue;
+            const long blocks = (long)ntile * (G / c) * ((n + r - 1) / r);
+            const long waves = (blocks + 2L * sms - 1) / (2L * sms);
+            const double cost = (double)waves * (std::min(n, r + 2 * H) + 0.5 * std::min(n, r)) * c;
+            if (!ok || cost < best) {
+                ok = true;
+                best = cost;
+                cw = c;
+                R = r;
+            }
+        }
+    return ok;
+}
+
+template <int CW, bool FIRST>
+void smooth2_allow_smem() {
+    MG_CUDA(cudaFuncSetAttribute(kb_smooth2<CW, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SMOOTH2_SMEM_MAX));
+}
+
 GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so,
                       const PcOperator* pco = nullptr) {
     auto* P = new GraphPlan();
@@ -1426,6 +1769,9 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
         P->rbs0 = so.rows_per_block;
         P->rbs1 = so.coarse_rows_per_block;
         P->base_tb = so.base_tiles;
+        P->hf = so.halo_fusion;
+        P->bc = so.base_cores;
+        P->base_cc = so.base_cores != MG_BASE_TENSOR;
         if (pco) {
             P->pc = true;
             P->pco = *pco;
@@ -1482,6 +1828,21 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
                 D.y = (float*)alloc(*P, e * 4);
             }
             if (d > 0) D.r = (float*)alloc(*P, e * 4);
+            // halo-fused kernels (two sweeps per launch, prolongation with residual
+            // update) on smoothed depths of shared operators
+            if (!P->pc && so.precond == MG_PRECOND_MULTIGRID && d + 1 < nd && so.halo_fusion != 1 &&
+                smooth2_shape(D.n, mm.ell_bw, ntile, c->sm_count > 0 ? c->sm_count : 1, D.f_cw, D.f_R)) {
+                D.f_H = mm.ell_bw;
+                D.f_nrb = (D.n + D.f_R - 1) / D.f_R;
+                smooth2_allow_smem<8, true>();
+                smooth2_allow_smem<8, false>();
+                smooth2_allow_smem<16, true>();
+                smooth2_allow_smem<16, false>();
+                MG_CUDA(cudaFuncSetAttribute(kb_prolong_res<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMOOTH2_SMEM_MAX));
+                MG_CUDA(cudaFuncSetAttribute(kb_prolong_res<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMOOTH2_SMEM_MAX));
+            }
             P->depth.push_back(D);
         }
         const size_t e0 = (size_t)ntile * m0.n * G;
@@ -1634,7 +1995,8 @@ void phi_batch_graph(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solv
         if (!q->pc && q->op == &op && q->ntile == ntile && q->precision == so.precision && q->precond == so.precond &&
             q->nu == smooth_sweeps(so) && q->omega == (so.omega > 0.0 ? (float)so.omega : 0.7f) &&
             q->smoother == so.smoother && q->cheb_ratio == so.cheb_ratio &&
-            q->rbs0 == so.rows_per_block && q->rbs1 == so.coarse_rows_per_block && q->base_tb == so.base_tiles) {
+            q->rbs0 == so.rows_per_block && q->rbs1 == so.coarse_rows_per_block && q->base_tb == so.base_tiles &&
+            q->hf == so.halo_fusion && q->bc == so.base_cores) {
             P = q;
             break;
         }

@@ -89,6 +89,7 @@ struct MeshLevel {
     // ELL view of the CSR pattern: width W, column-major (entry w of row i at w * n + i);
     // padding entries point at the row itself with slot -1
     int ell_W = 0;
+    int ell_bw = 0;             // bandwidth max |i - j| over the pattern (padding included)
     DBuf ell_col, ell_slot;     // int32 W x n
     // one refinement step to the coarse parent mesh (if any): P with <= 2 entries per fine row
     int parent_mesh = -1;
@@ -168,7 +169,7 @@ struct mg_ctx {
     std::vector<NewtonPlan*> nplans;  // Newton-step plans (own their per-column PCG graphs)
     std::map<int, NlMesh*> nl;       // mesh -> static data of its nonlinear elements
     struct Shape {                   // launch shape chosen by mg_autotune
-        int path, tile, cluster, rbs0, rbs1, base_tiles;
+        int path, tile, cluster, rbs0, rbs1, base_tiles, hf, bc;
         double ms;
     };
     std::map<std::pair<int, int>, Shape> tuned;  // (mesh, column bucket) -> shape

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <set>
 #include <vector>
 
 #include "internal.h"
@@ -482,7 +483,8 @@ void check_solver_opts(const mg_solver_opts& so) {
         !(so.coarse_rows_per_block == 0 || (so.coarse_rows_per_block >= 16 && so.coarse_rows_per_block <= 4096)) ||
         !(so.base_tiles == 0 || so.base_tiles == 1 || so.base_tiles == 2 || so.base_tiles == 4) ||
         (so.smoother != MG_SMOOTH_CHEBYSHEV && so.smoother != MG_SMOOTH_JACOBI) ||
-        !(so.cheb_ratio == 0.0 || (so.cheb_ratio > 1.0 && so.cheb_ratio <= 1e4)))
+        !(so.cheb_ratio == 0.0 || (so.cheb_ratio > 1.0 && so.cheb_ratio <= 1e4)) || so.halo_fusion < 0 ||
+        so.halo_fusion > 2 || so.base_cores < 0 || so.base_cores > 2)
         mg_fail(MG_EINVAL, "bad solver options");
 }
 
@@ -574,6 +576,100 @@ mg_status sequential_impl(mg_ctx* c, int level, int64_t N, double T, const doubl
     return MG_OK;
 }
 
+// Sizes of an MGRIT solve's level storage (one pooled allocation, carved in this
+// order): per level with a coarsening factor m the iterate U (m slabs of n x ld),
+// the FAS right-hand side G (not on level 0), the C-point residual R and the
+// values Phi(u) V (n x ld each); the coarsest level U and G time-major; every level
+// below the finest also W, g2 and Vc (n x ldw each).
+std::vector<size_t> level_storage(const std::vector<Level>& lv) {
+    std::vector<size_t> sizes;
+    auto plan = [&](int64_t nd) { sizes.push_back((size_t)nd * sizeof(double)); };
+    for (int l = 0; l < (int)lv.size(); ++l) {
+        const Level& L = lv[l];
+        if (L.m) {
+            plan(L.m * L.n * L.ld);          // U
+            plan(l ? L.m * L.n * L.ld : 0);  // G
+            plan(L.n * L.ld);                // R
+            plan(L.n * L.ld);                // V
+        } else {
+            plan((L.N + 1) * L.n);  // U
+            plan((L.N + 1) * L.n);  // G
+            plan(0);
+            plan(0);
+        }
+        for (int q = 0; q < 3; ++q) plan(l > 0 ? L.n * L.ldw : 0);  // W, g2, Vc
+    }
+    return sizes;
+}
+
+// Device bytes of the graph-path plan of a linear batched step of kpad columns on
+// a mesh whose multigrid depths have n[0] (finest) .. n[nd-1] (base) rows: the
+// FP32 V-cycle vectors (x on every depth, four K-split copies on the base; s, s',
+// y below the base; r below the finest) and the Krylov vectors of the finest depth.
+size_t graph_plan_bytes(const std::vector<int64_t>& n, int64_t kpad, int precision) {
+    size_t b = 0;
+    const int nd = (int)n.size();
+    for (int d = 0; d < nd; ++d) {
+        const int vecs = (d + 1 == nd ? (nd > 1 ? 4 : 1) : 4) + (d > 0 ? 1 : 0);
+        b += (size_t)vecs * kpad * n[d] * sizeof(float);
+    }
+    b += (size_t)kpad * n[0] * (precision == MG_FP64 ? 4 * 8 + 4 : 2 * 8 + 4 * 4);
+    return b;
+}
+
+// Estimated device bytes an MGRIT solve of N steps with options o allocates in the
+// context: the level storage (exact) and the step plans of its relaxation batches
+// (one per level and batch width; Newton plans add the per-column Jacobians, their
+// FP32 copies and scaled values on every depth and the banded base factor).
+size_t mgrit_work_estimate(mg_ctx* c, int64_t N, const mg_opts& o) {
+    if (N <= 0 || o.levels < 1 || o.levels > 8) mg_fail(MG_EINVAL, "bad solve arguments");
+    for (int l = 0; l < o.levels; ++l)
+        if (o.space_level[l] < 0 || o.space_level[l] >= (int)c->meshes.size()) mg_fail(MG_EINVAL, "bad space level");
+    std::vector<Level> lv(o.levels);
+    int64_t stride = 1;
+    for (int l = 0; l < o.levels; ++l) {
+        Level& L = lv[l];
+        L.mesh = o.space_level[l];
+        L.n = c->meshes[L.mesh].n;
+        L.N = N / stride;
+        if (l < o.levels - 1 && o.levels > 1) {
+            L.m = std::max(1, o.m[l]);
+            L.NT = L.N / L.m;
+            L.ld = round_up(L.NT + 1, 4);
+            stride *= L.m;
+        }
+        if (l > 0) L.ldw = round_up(L.N + 1, 4);
+    }
+    size_t bytes = 0;
+    if (o.levels > 1)
+        for (auto s : level_storage(lv)) bytes += s;
+    // one batched-step plan per (mesh, batch width) the solve relaxes with
+    std::set<std::pair<int, int64_t>> shapes;
+    for (int l = 0; l < o.levels; ++l) {
+        const int64_t k = o.levels > 1 && l < o.levels - 1 ? lv[l].NT : 1;
+        shapes.insert({lv[l].mesh, (k + 15) / 16 * 16});
+    }
+    for (const auto& sh : shapes) {
+        if (sh.second < MG_GRAPH_MIN_COLUMNS) continue;  // cluster path: small shared work vectors
+        std::vector<int64_t> n;
+        std::vector<int> bw;
+        for (int m = sh.first; m >= 0; m = c->meshes[m].parent_mesh) {
+            n.push_back(c->meshes[m].n);
+            bw.push_back(c->meshes[m].ell_bw);
+            if (o.solver.precond != MG_PRECOND_MULTIGRID) break;
+        }
+        bytes += graph_plan_bytes(n, sh.second, o.solver.precision);
+        if (mesh_is_nonlinear(c, sh.first)) {
+            int64_t rows = 0;
+            for (auto x : n) rows += x;
+            const int W = c->meshes[sh.first].ell_W;
+            bytes += (size_t)sh.second * rows * (W * (8 + 4 + 4) + 16);
+            bytes += (size_t)sh.second * n.back() * (2 * bw.back() + 1) * sizeof(float) * 2;
+        }
+    }
+    return bytes;
+}
+
 mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* out, const mg_opts* opts,
                      mg_stats* stats) {
     mg_opts o;
@@ -626,34 +722,10 @@ mg_status solve_impl(mg_ctx* c, int64_t N, double T, const double* a0, double* o
         }
     }
     // storage
-    size_t bytes = 0;
-    std::vector<size_t> sizes;
-    auto plan = [&](size_t nd) { sizes.push_back(nd * sizeof(double)); };
-    for (int l = 0; l < o.levels; ++l) {
-        Level& L = S.lv[l];
-        if (L.m) {
-            plan(L.m * L.n * L.ld);                 // U
-            plan(l ? L.m * L.n * L.ld : 0);         // G
-            plan(L.n * L.ld);                       // R
-            plan(L.n * L.ld);                       // V
-        } else {
-            plan((L.N + 1) * L.n);                  // U
-            plan((L.N + 1) * L.n);                  // G
-            plan(0);
-            plan(0);
-        }
-        if (l > 0) {
-            L.ldw = round_up(L.N + 1, 4);
-            plan(L.n * L.ldw);  // W
-            plan(L.n * L.ldw);  // g2
-            plan(L.n * L.ldw);  // Vc
-        } else {
-            plan(0);
-            plan(0);
-            plan(0);
-        }
-    }
+    for (int l = 1; l < o.levels; ++l) S.lv[l].ldw = round_up(S.lv[l].N + 1, 4);
+    std::vector<size_t> sizes = level_storage(S.lv);
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t bytes = 0;
     for (auto s : sizes) bytes += r256(s);
     bytes += r256(S.kRedBlocks * sizeof(double)) + r256(sizeof(double));
     // one pooled allocation, carved per level
@@ -916,6 +988,29 @@ mg_status mg_sequential(mg_ctx* c, int level, int64_t N, double T, const double*
 mg_status mg_solve(mg_ctx* c, int64_t N, double T, const double* a0, double* out, const mg_opts* opts,
                    mg_stats* stats) {
     return run(c, [&]() { return solve_impl(c, N, T, a0, out, opts, stats); });
+}
+
+mg_status mg_solve_work_bytes(mg_ctx* c, int64_t N, const mg_opts* opts, int64_t* bytes) {
+    return run(c, [&]() -> mg_status {
+        if (!bytes) mg_fail(MG_EINVAL, "mg_solve_work_bytes: bad arguments");
+        mg_opts o;
+        if (opts) o = *opts;
+        else mg_opts_defaults(&o);
+        *bytes = (int64_t)mgrit_work_estimate(c, N, o);
+        return MG_OK;
+    });
+}
+
+mg_status mg_release_work(mg_ctx* c) {
+    return run(c, [&]() -> mg_status {
+        MG_CUDA(cudaStreamSynchronize(c->stream));
+        ctx_drop_plans(c);
+        for (auto& b : c->solve_buf) b.release();
+        for (auto& b : c->ws) b.release();
+        c->host_in.release();
+        c->host_out.release();
+        return MG_OK;
+    });
 }
 
 mg_status mg_solve_host(mg_ctx* c, int64_t N, double T, const double* a0_host, double* out_host, const mg_opts* opts,

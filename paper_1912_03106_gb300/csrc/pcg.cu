@@ -1089,7 +1089,7 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
         return;
     }
     if (so.path == MG_PATH_AUTO && so.tile == 0 && so.cluster == 0 && so.rows_per_block == 0 &&
-        so.coarse_rows_per_block == 0 && so.base_tiles == 0) {
+        so.coarse_rows_per_block == 0 && so.base_tiles == 0 && so.halo_fusion == 0 && so.base_cores == 0) {
         // a launch shape mg_autotune recorded for this mesh and tile count
         auto it = c->tuned.find({op.mesh, tune_bucket(io.k)});
         if (it != c->tuned.end()) {
@@ -1100,6 +1100,8 @@ void phi_batch(mg_ctx* c, const StepOp& op, const PhiIO& io, const mg_solver_opt
             t.rows_per_block = it->second.rbs0;
             t.coarse_rows_per_block = it->second.rbs1;
             t.base_tiles = it->second.base_tiles;
+            t.halo_fusion = it->second.hf;
+            t.base_cores = it->second.bc;
             phi_batch(c, op, io, t, counters);
             return;
         }

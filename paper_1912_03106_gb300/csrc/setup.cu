@@ -412,6 +412,7 @@ static void build_pattern(MeshLevel& m) {
             bool real = sl < m.rowptr_h[i + 1];
             ec[(size_t)w * m.n + i] = real ? m.col_h[sl] : (int32_t)i;
             es[(size_t)w * m.n + i] = real ? sl : -1;
+            m.ell_bw = std::max(m.ell_bw, (int)std::abs(ec[(size_t)w * m.n + i] - (int32_t)i));
         }
     upload(m.ell_col, ec);
     upload(m.ell_slot, es);

@@ -3,8 +3,9 @@
 // The step's work per PCG iteration is fixed by the method; what the hardware
 // makes of it depends on the launch shape: on the cluster path the column tile
 // width and the CTAs per cluster, on the graph path the rows each block owns on
-// the finest and on the coarser multigrid depths (grid size against the 152 SMs)
-// and the column tiles per block of the dense base solve.  mg_autotune times
+// the finest and on the coarser multigrid depths (grid size against the 152 SMs),
+// halo-fused multigrid kernels or not, and the cores (CUDA or tensor) and column
+// tiles per block of the dense base solve.  mg_autotune times
 // one batched step per candidate shape with CUDA events and keeps the fastest,
 // by coordinate descent from the library's own choice.
 #include <cuda_runtime.h>
@@ -32,7 +33,7 @@ __global__ void kt_fill(int64_t n, double* x) {
 }
 
 struct Trial {
-    int path, tile, cluster, rbs0, rbs1, tb;
+    int path, tile, cluster, rbs0, rbs1, tb, hf, bc;
 };
 
 }  // namespace
@@ -89,9 +90,12 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
                 so.rows_per_block = t.rbs0;
                 so.coarse_rows_per_block = t.rbs1;
                 so.base_tiles = t.tb;
+                so.halo_fusion = t.hf;
+                so.base_cores = t.bc;
                 if (mg_trace_level() >= 3) {
-                    std::fprintf(stderr, "[autotune] mesh %d k %d path %d tile %d cluster %d rbs %d/%d tiles %d\n",
-                                 A.level, A.k, t.path, t.tile, t.cluster, t.rbs0, t.rbs1, t.tb);
+                    std::fprintf(stderr,
+                                 "[autotune] mesh %d k %d path %d tile %d cluster %d rbs %d/%d tiles %d halo %d base %d\n",
+                                 A.level, A.k, t.path, t.tile, t.cluster, t.rbs0, t.rbs1, t.tb, t.hf, t.bc);
                     MG_CUDA(cudaStreamSynchronize(s));
                 }
                 phi_batch(c, op, io, so, nullptr);  // builds the plan, warms the caches
@@ -116,9 +120,9 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
             try {
                 if (A.k < 32) {  // latency-bound: cluster tile width and size, or the graph path
                     for (int tile : {1, 8, 16})
-                        for (int cl : {8, 16}) consider({MG_PATH_CLUSTER, tile, cl, 0, 0, 0});
+                        for (int cl : {8, 16}) consider({MG_PATH_CLUSTER, tile, cl, 0, 0, 0, 0, 0});
                 }
-                Trial gb{MG_PATH_GRAPH, 0, 0, 0, 0, 0};
+                Trial gb{MG_PATH_GRAPH, 0, 0, 0, 0, 0, 0, 0};
                 double gt = time_of(gb);
                 for (int r0 : {128, 256, 512, 1024}) {
                     Trial t = gb;
@@ -126,9 +130,21 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
                     const double ms = time_of(t);
                     if (ms < gt) gt = ms, gb = t;
                 }
+                for (int hf : {1, 2}) {
+                    Trial t = gb;
+                    t.hf = hf;
+                    const double ms = time_of(t);
+                    if (ms < gt) gt = ms, gb = t;
+                }
                 for (int r1 : {32, 64, 128, 256}) {
                     Trial t = gb;
                     t.rbs1 = r1;
+                    const double ms = time_of(t);
+                    if (ms < gt) gt = ms, gb = t;
+                }
+                for (int bc : {MG_BASE_CUDA, MG_BASE_TENSOR}) {
+                    Trial t = gb;
+                    t.bc = bc;
                     const double ms = time_of(t);
                     if (ms < gt) gt = ms, gb = t;
                 }
@@ -154,7 +170,10 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
             A.opts->rows_per_block = best.rbs0;
             A.opts->coarse_rows_per_block = best.rbs1;
             A.opts->base_tiles = best.tb;
-            c->tuned[{A.level, tune_bucket(A.k)}] = {best.path, best.tile, best.cluster, best.rbs0, best.rbs1, best.tb, best_t};
+            A.opts->halo_fusion = best.hf;
+            A.opts->base_cores = best.bc;
+            c->tuned[{A.level, tune_bucket(A.k)}] = {best.path, best.tile, best.cluster, best.rbs0, best.rbs1,
+                                                     best.tb,   best.hf,   best.bc,      best_t};
             if (A.best_ms) *A.best_ms = best_t;
         },
         &a);

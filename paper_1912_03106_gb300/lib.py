@@ -56,6 +56,8 @@ class mg_solver_opts(C.Structure):
         ("base_tiles", C.c_int),
         ("smoother", C.c_int),
         ("cheb_ratio", C.c_double),
+        ("halo_fusion", C.c_int),
+        ("base_cores", C.c_int),
     ]
 
 
@@ -130,8 +132,10 @@ _SIGNATURES = {
     "mg_joule_losses": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P]),
     "mg_autotune": (C.c_int, [_P, C.c_int, _I64, _D, C.c_int, C.POINTER(mg_solver_opts), C.POINTER(_D)]),
     "mg_batch_solve": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_I64), C.POINTER(_D), C.POINTER(_P),
-                                 C.POINTER(_P), C.POINTER(mg_opts), C.c_int, C.POINTER(C.c_int),
+                                 C.POINTER(_P), C.POINTER(mg_opts), C.c_int, _I64, C.POINTER(C.c_int),
                                  C.POINTER(mg_stats)]),
+    "mg_solve_work_bytes": (C.c_int, [_P, _I64, C.POINTER(mg_opts), C.POINTER(_I64)]),
+    "mg_release_work": (C.c_int, [_P]),
 }
 
 EXPORTED = tuple(_SIGNATURES)

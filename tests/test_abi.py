@@ -50,6 +50,7 @@ def test_defaults_are_sane(libpath):
     assert so.cg_tol == 1e-13 and so.max_cg > 0 and so.precision == lib.MG_FP64
     # the last fields: a binding whose layout drifted from the header reads garbage here
     assert so.smoother == 0 and so.cheb_ratio == 30.0 and so.smooth == 5 and so.base_tiles == 0
+    assert so.halo_fusion == 0 and so.base_cores == 0
     o = lib.mg_opts()
     L.mg_opts_defaults(ctypes.byref(o))
     assert o.levels == 2 and o.m[0] == 16 and o.relax == 1 and o.restrict_mode == 2
@@ -117,6 +118,38 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_struct_layout_matches_binding(tmp_path):
+    """The ctypes structures of the binding have the header's size and field
+    offsets (a C program built with the header prints them)."""
+    import shutil
+    import subprocess
+
+    from paper_1912_03106_gb300 import lib
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"mg_solver_opts": lib.mg_solver_opts, "mg_opts": lib.mg_opts, "mg_stats": lib.mg_stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "mgrit_em.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('    printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f in cls._fields_:
+            lines.append('    printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {(w[0], w[1]): int(w[2]) for w in (x.split() for x in out) if len(w) == 3}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
 
 
 def test_null_context_is_rejected(libpath):

@@ -145,6 +145,61 @@ def test_batch_solve_matches_oracle(meshes):
         ctx.close()
 
 
+def test_batch_solve_under_a_work_budget(meshes):
+    """With a work budget smaller than any two instances' work buffers the
+    scheduler runs the instances one at a time (largest first) and frees each
+    one's buffers when it ends: the trajectories are the unbounded call's, bit for
+    bit, and the contexts hold no work buffers afterwards."""
+    insts = instances(5, seed=7, mesh_levels=(0, 1), Ns=(64, 128, 256), T=2.5e-3, nonlinear_fraction=0.2,
+                      nonlinear_levels=(0,))
+    setups = [instance_setup(meshes, inst, torch.cuda.Stream()) for inst in insts]
+    torch.cuda.synchronize()
+    args = ([s[0] for s in setups], [i.N for i in insts], [i.T for i in insts], [s[2] for s in setups],
+            [s[3] for s in setups], [s[1] for s in setups])
+    rc, status, _ = api.mg_batch_solve(*args)
+    assert rc == 0, status
+    free = [s[3].clone() for s in setups]
+    est = [ctx.mg_solve_work_bytes(inst.N, opts) for (ctx, opts, _, _), inst in zip(setups, insts)]
+    assert all(e > 0 for e in est)
+    for s in setups:
+        s[3].zero_()
+    torch.cuda.synchronize()
+    rc, status, stats = api.mg_batch_solve(*args, work_budget=min(est) + 1)
+    assert rc == 0, status
+    torch.cuda.synchronize()
+    for s, f in zip(setups, free):
+        assert torch.equal(s[3], f)
+    for s in setups:
+        s[0].close()
+
+
+def test_work_estimate_covers_a_solve(meshes):
+    """mg_solve_work_bytes against the device memory one solve actually takes
+    (free memory before and after, with the step operators already built and the
+    work buffers released): the estimate is within [0.75, 2] of it, and
+    mg_release_work gives the memory back."""
+    model = machine_model(pwm=PwmSpec(J0=1e6, f_carrier=20e3))
+    ctx, ids = make_ctx(meshes, model)
+    N, T = 1024, 5e-3
+    n = ctx.mg_num_dofs(ids[2])
+    a0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = torch.zeros((N + 1, n), dtype=torch.float64, device="cuda")
+    opts = api.mgrit_opts(levels=3, m=(16, 16), space_level=(ids[2], ids[0], ids[0]), relax=1, tol=1e-6)
+    ctx.mg_solve(N, T, a0, out, opts)
+    ctx.mg_release_work()
+    torch.cuda.synchronize()
+    before = torch.cuda.mem_get_info()[0]
+    ctx.mg_solve(N, T, a0, out, opts)
+    torch.cuda.synchronize()
+    used = before - torch.cuda.mem_get_info()[0]
+    est = ctx.mg_solve_work_bytes(N, opts)
+    assert used > 0 and 0.75 * used <= est <= 2.0 * used, (used, est)
+    ctx.mg_release_work()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= before - (8 << 20)
+    ctx.close()
+
+
 def test_batch_solve_rejects_repeated_context(meshes):
     inst = instances(1, seed=0, mesh_levels=(0,), Ns=(64,), T=2.5e-3, nonlinear_fraction=0.0)[0]
     ctx, opts, a0, out = instance_setup(meshes, inst, torch.cuda.Stream())
