@@ -128,7 +128,8 @@ def parse():
     ap.add_argument("--reps", type=int, default=2, help="with --profile-step: number of steps")
     ap.add_argument("--level", type=int, default=2, help="with --profile-step: mesh level 0..3 (18,240 DOFs = 2)")
     ap.add_argument("--halo-fusion", type=int, default=0,
-                    help="with --profile-step: halo-fused multigrid kernels (0 library choice, 1 off, 2 on)")
+                    help="with --profile-step: halo-fused multigrid kernels (0 library choice, 1 off, 2 on, "
+                         "3 on with the sweeps' input staged in shared memory)")
     ap.add_argument("--base-cores", type=int, default=0,
                     help="with --profile-step: dense base solve on CUDA (1) or tensor (2) cores, 0 library choice")
     ap.add_argument("--tol", type=float, default=0.0,

@@ -207,8 +207,9 @@ typedef struct {
                                   intermediate vector in shared memory on a halo of the
                                   operator's bandwidth (two consecutive smoothing sweeps per
                                   launch; the prolongation with the residual update), where the
-                                  halo fits; 1 = one kernel per sweep and per transfer;
-                                  0 = library choice (2).  Same arithmetic either way. */
+                                  halo fits; 3 = as 2, and the sweeps' input vector is staged
+                                  in shared memory too; 1 = one kernel per sweep and per
+                                  transfer; 0 = library choice (2).  Same arithmetic in all. */
     int base_cores;            /* graph path, linear steps: the dense base solve x = A^-1 r of
                                   the V-cycle on MG_BASE_CUDA (FP32 FMA) or MG_BASE_TENSOR
                                   (3xTF32 mma.sync, FP32-level accuracy) cores, 0 = library

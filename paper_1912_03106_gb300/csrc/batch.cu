@@ -106,10 +106,11 @@ struct Depth {
     // per column tile: 0 once all of its columns have stopped iterating; the PCG and
     // multigrid kernels then skip the tile (its vectors and partials stay as they are)
     const int* tact;
-    // two smoothing sweeps per launch (kb_smooth2): columns and rows per block, the
-    // operator's bandwidth max |i - j| and the row blocks per column group; f_cw = 0:
-    // one sweep per launch
-    int f_cw, f_R, f_H, f_nrb;
+    // halo-fused kernels (kb_smooth2, kb_prolong_res): columns and rows per block,
+    // the operator's bandwidth max |i - j|, the row blocks per column group and
+    // whether the sweeps' input is staged in shared memory too; f_cw = 0: one
+    // sweep and one transfer per launch
+    int f_cw, f_R, f_H, f_nrb, f_stage;
 };
 
 struct Cols {
@@ -746,12 +747,49 @@ __global__ void __launch_bounds__(NTB, minb_s<PC>()) kb_smooth(Depth D, const fl
 // every row within the operator's bandwidth H of its own rows, [a - H, a + R + H),
 // reading s0 through L2, so that the second sweep gathers s1 from shared memory and
 // s1 never leaves the SM; the halo rows' first sweep is done by both neighbouring
-// blocks.  Same arithmetic, in the same order, as kb_smooth_first / kb_smooth.
+// blocks.  STAGE: s0 itself is first copied into shared memory on the rows within
+// 2H of the block's rows (coalesced streaming loads), so that the first sweep too
+// gathers from shared memory.  Same arithmetic, in the same order, as
+// kb_smooth_first / kb_smooth.
 constexpr int NT2 = 512;
-template <int CW, bool FIRST>
+
+// row product acc[e] = sum_w LD[w, i] v[col[w, i] - lo][e] over a shared-memory vector
+template <int TPR>
+__device__ __forceinline__ void ell_row_sh(const Depth& D, int i, const float4* v, int lo, int l, float (&acc)[VF]) {
+#pragma unroll
+    for (int e = 0; e < VF; ++e) acc[e] = 0.0f;
+    int j[WMAX];
+    float a[WMAX];
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < D.W) {
+            j[w] = __ldg(D.col + w * D.n + i);
+            a[w] = __ldg(D.LD32 + w * D.n + i);
+        }
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < D.W) {
+            const float4 sj = v[(j[w] - lo) * TPR + l];
+            acc[0] += a[w] * sj.x;
+            acc[1] += a[w] * sj.y;
+            acc[2] += a[w] * sj.z;
+            acc[3] += a[w] * sj.w;
+        }
+    for (int w = WMAX; w < D.W; ++w) {
+        const float4 sj = v[(__ldg(D.col + w * D.n + i) - lo) * TPR + l];
+        const float aw = __ldg(D.LD32 + w * D.n + i);
+        acc[0] += aw * sj.x;
+        acc[1] += aw * sj.y;
+        acc[2] += aw * sj.z;
+        acc[3] += aw * sj.w;
+    }
+}
+
+template <int CW, bool FIRST, bool STAGE>
 __global__ void __launch_bounds__(NT2, 2) kb_smooth2(Depth D, const float* s0_base, float* dst_base, float wa,
                                                      float wb) {
-    extern __shared__ float4 s1sh[];  // (R + 2H) rows x CW floats
+    // shared memory: STAGE: s0 on (R + 4H) rows, then s1 on (R + 2H) rows; else s1 only
+    extern __shared__ float4 sh2[];
     constexpr int TPR = CW / VF, RPP = NT2 / TPR, NSUB = G / CW;
     phase_begin();
     const int rb = blockIdx.x % D.f_nrb;
@@ -762,11 +800,31 @@ __global__ void __launch_bounds__(NT2, 2) kb_smooth2(Depth D, const float* s0_ba
     const int c0 = (grp % NSUB) * CW + l * VF;
     const int a = rb * D.f_R, b = min(D.n, a + D.f_R);
     const int lo = max(0, a - D.f_H), hi = min(D.n, b + D.f_H);
+    const int lo0 = max(0, a - 2 * D.f_H), hi0 = min(D.n, b + 2 * D.f_H);
     const float* s0 = tv(s0_base, D.n, t);
+    float4* s0sh = sh2;
+    float4* s1sh = STAGE ? sh2 + (size_t)(D.f_R + 4 * D.f_H) * TPR : sh2;
+    if constexpr (STAGE) {
+        for (int i = lo0 + (int)threadIdx.x / TPR; i < hi0; i += RPP) {
+            float sv[VF];
+            vld<float, VF>(s0 + i * G + c0, sv);
+            s0sh[(i - lo0) * TPR + l] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+        }
+        __syncthreads();
+    }
     for (int i = lo + (int)threadIdx.x / TPR; i < hi; i += RPP) {
         float sv[VF], acc[VF];
-        vld<float, VF>(s0 + i * G + c0, sv);
-        ell_vec_w<VF, float, float, float, false>(D.col, D.LD32, D.n, D.W, i, s0, c0, acc);
+        if constexpr (STAGE) {
+            const float4 v = s0sh[(i - lo0) * TPR + l];
+            sv[0] = v.x;
+            sv[1] = v.y;
+            sv[2] = v.z;
+            sv[3] = v.w;
+            ell_row_sh<TPR>(D, i, s0sh, lo0, l, acc);
+        } else {
+            vld<float, VF>(s0 + i * G + c0, sv);
+            ell_vec_w<VF, float, float, float, false>(D.col, D.LD32, D.n, D.W, i, s0, c0, acc);
+        }
         float4 o;
         o.x = sv[0] - wa * acc[0];
         o.y = sv[1] - wa * acc[1];
@@ -781,7 +839,15 @@ __global__ void __launch_bounds__(NT2, 2) kb_smooth2(Depth D, const float* s0_ba
         const float4 s1v = s1sh[(i - lo) * TPR + l];
         const float s1[VF] = {s1v.x, s1v.y, s1v.z, s1v.w};
         float sv[VF], xv[VF];
-        vld<float, VF>(s0 + i * G + c0, sv);
+        if constexpr (STAGE) {
+            const float4 v = s0sh[(i - lo0) * TPR + l];
+            sv[0] = v.x;
+            sv[1] = v.y;
+            sv[2] = v.z;
+            sv[3] = v.w;
+        } else {
+            vld<float, VF>(s0 + i * G + c0, sv);
+        }
         const float di = __ldg(D.dinv32 + i);
         if constexpr (FIRST) {
 #pragma unroll
@@ -795,32 +861,8 @@ __global__ void __launch_bounds__(NT2, 2) kb_smooth2(Depth D, const float* s0_ba
         for (int e = 0; e < VF; ++e) xv[e] = xv[e] + wb * di * s1[e];
         vst<float, VF>(x + i * G + c0, xv);
         if (dst) {
-            float acc[VF] = {0.0f, 0.0f, 0.0f, 0.0f};
-            int j[WMAX];
-            float v[WMAX];
-#pragma unroll
-            for (int w = 0; w < WMAX; ++w)
-                if (w < D.W) {
-                    j[w] = __ldg(D.col + w * D.n + i);
-                    v[w] = __ldg(D.LD32 + w * D.n + i);
-                }
-#pragma unroll
-            for (int w = 0; w < WMAX; ++w)
-                if (w < D.W) {
-                    const float4 sj = s1sh[(j[w] - lo) * TPR + l];
-                    acc[0] += v[w] * sj.x;
-                    acc[1] += v[w] * sj.y;
-                    acc[2] += v[w] * sj.z;
-                    acc[3] += v[w] * sj.w;
-                }
-            for (int w = WMAX; w < D.W; ++w) {
-                const float4 sj = s1sh[(__ldg(D.col + w * D.n + i) - lo) * TPR + l];
-                const float vw = __ldg(D.LD32 + w * D.n + i);
-                acc[0] += vw * sj.x;
-                acc[1] += vw * sj.y;
-                acc[2] += vw * sj.z;
-                acc[3] += vw * sj.w;
-            }
+            float acc[VF];
+            ell_row_sh<TPR>(D, i, s1sh, lo, l, acc);
             float so[VF];
 #pragma unroll
             for (int e = 0; e < VF; ++e) so[e] = s1[e] - wb * acc[e];
@@ -1337,9 +1379,20 @@ struct VecOf {
     static constexpr int V = std::is_same<T, double>::value ? 2 : 4;
 };
 
-// p = z + beta p, q = L z + beta q, partial (p, q)
+// p = z + beta p, q = L z + beta q, partial (p, q).  The FP64 form on a shared
+// operator is bound by GB300's FP64 pipe; 4 resident blocks per SM (64 registers)
+// keep more FP64 instructions in flight than the 3 that 76 registers allowed.
+// Per-column operators (several values per entry and lane) keep the 3 (FP64) or 2
+// (FP32, four values) blocks their registers allowed without a bound.
+#ifndef MG_MINB_A
+#define MG_MINB_A 4
+#endif
 template <class T, bool PC>
-__global__ void __launch_bounds__(NTB) kb_pcg_a(Depth D, const T* Lv, T* p_base, T* q_base, const double* beta,
+__host__ __device__ constexpr int minb_a() {
+    return PC ? (std::is_same<T, double>::value ? 3 : 2) : MG_MINB_A;
+}
+template <class T, bool PC>
+__global__ void __launch_bounds__(NTB, minb_a<T, PC>()) kb_pcg_a(Depth D, const T* Lv, T* p_base, T* q_base, const double* beta,
                                                 double* part) {
     phase_begin();
     constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
@@ -1531,18 +1584,28 @@ void* alloc(GraphPlan& P, size_t bytes) {
 inline unsigned grid(int ntile, int nrb) { return (unsigned)(ntile * nrb); }
 
 
+// shared memory of kb_smooth2 (s1 on R + 2H rows; staged: also s0 on R + 4H rows)
+inline size_t smooth2_smem(int R, int H, int cw, bool stage) {
+    return (size_t)((R + 2 * H) + (stage ? R + 4 * H : 0)) * cw * sizeof(float);
+}
+
 template <bool FIRST>
 void smooth2_launch(GraphPlan& P, const Depth& D, cudaStream_t s, const float* src, float* dst, float wa, float wb) {
     const unsigned g = (unsigned)(P.ntile * (G / D.f_cw) * D.f_nrb);
-    const size_t smem = (size_t)(D.f_R + 2 * D.f_H) * D.f_cw * sizeof(float);
-    if (D.f_cw == 8) pdl_launch(kb_smooth2<8, FIRST>, g, NT2, smem, s, D, src, dst, wa, wb);
-    else pdl_launch(kb_smooth2<16, FIRST>, g, NT2, smem, s, D, src, dst, wa, wb);
+    const size_t smem = smooth2_smem(D.f_R, D.f_H, D.f_cw, D.f_stage);
+    if (D.f_stage) {
+        if (D.f_cw == 8) pdl_launch(kb_smooth2<8, FIRST, true>, g, NT2, smem, s, D, src, dst, wa, wb);
+        else pdl_launch(kb_smooth2<16, FIRST, true>, g, NT2, smem, s, D, src, dst, wa, wb);
+    } else {
+        if (D.f_cw == 8) pdl_launch(kb_smooth2<8, FIRST, false>, g, NT2, smem, s, D, src, dst, wa, wb);
+        else pdl_launch(kb_smooth2<16, FIRST, false>, g, NT2, smem, s, D, src, dst, wa, wb);
+    }
 }
 
 void prolong_res_launch(GraphPlan& P, const Depth& D, const Depth& C, cudaStream_t s, int parts, size_t pstride,
                         float* sv) {
     const unsigned g = (unsigned)(P.ntile * (G / D.f_cw) * D.f_nrb);
-    const size_t smem = (size_t)(D.f_R + 2 * D.f_H) * D.f_cw * sizeof(float);
+    const size_t smem = smooth2_smem(D.f_R, D.f_H, D.f_cw, false);
     if (D.f_cw == 8) pdl_launch(kb_prolong_res<8>, g, NT2, smem, s, D, C, parts, pstride, sv);
     else pdl_launch(kb_prolong_res<16>, g, NT2, smem, s, D, C, parts, pstride, sv);
 }
@@ -1727,23 +1790,24 @@ cudaGraphConditionalHandle new_handle(cudaStream_t s) {
 }
 
 // Launch shape of kb_smooth2 on a depth of n rows with bandwidth H over ntile
-// column tiles: columns (8 or 16) and rows per block such that two blocks of NT2
-// threads fit an SM (shared memory (R + 2H) CW floats each) and the halo is at
-// most 60 % of a block's rows (beyond that two single sweeps are cheaper); among
-// those the one with the least first-sweep work per SM (waves x halo-extended rows
-// x columns).  False if none qualifies.
+// column tiles: columns (8 or 16) and rows per block such that two
+// blocks of NT2 threads fit an SM (shared memory smooth2_smem each) and the halo is
+// at most 60 % of a block's rows (beyond that two single sweeps are cheaper); among
+// those the one with the least work per SM.  The first sweep is bound by L1
+// throughput (its gathers); a warp's gather costs one L1 wavefront per 128-byte
+// line it touches, so a row costs the same for 8 and 16 columns (8-column blocks
+// use half of each line), and the cost is waves x (halo-extended rows + half the
+// block's own rows for the second sweep).  False if none qualifies.
 constexpr size_t SMOOTH2_SMEM_MAX = 113 * 1024;
-bool smooth2_shape(int n, int H, int ntile, int sms, int& cw, int& R) {
+bool smooth2_shape(int n, int H, int ntile, int sms, bool stage, int& cw, int& R) {
     double best = 0.0;
     bool ok = false;
-    for (int c : {8, 16})
+    for (int c : {16, 8})  // ties go to 16 columns: half the blocks for the same time
         for (int r : {2048, 1536, 1024, 768, 512, 384, 256}) {
-            if (2.0 * H > 0.6 * r) continue;
-            const size_t smem = (size_t)(r + 2 * H) * c * sizeof(float);
-            if (smem > SMOOTH2_SMEM_MAX) continue;
+            if (2.0 * H > 0.6 * r || smooth2_smem(r, H, c, stage) > SMOOTH2_SMEM_MAX) continue;
             const long blocks = (long)ntile * (G / c) * ((n + r - 1) / r);
             const long waves = (blocks + 2L * sms - 1) / (2L * sms);
-            const double cost = (double)waves * (std::min(n, r + 2 * H) + 0.5 * std::min(n, r)) * c;
+            const double cost = (double)waves * (std::min(n, r + 2 * H) + 0.5 * std::min(n, r));
             if (!ok || cost < best) {
                 ok = true;
                 best = cost;
@@ -1754,9 +1818,9 @@ bool smooth2_shape(int n, int H, int ntile, int sms, int& cw, int& R) {
     return ok;
 }
 
-template <int CW, bool FIRST>
+template <int CW, bool FIRST, bool STAGE>
 void smooth2_allow_smem() {
-    MG_CUDA(cudaFuncSetAttribute(kb_smooth2<CW, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    MG_CUDA(cudaFuncSetAttribute(kb_smooth2<CW, FIRST, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SMOOTH2_SMEM_MAX));
 }
 
@@ -1830,14 +1894,20 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             if (d > 0) D.r = (float*)alloc(*P, e * 4);
             // halo-fused kernels (two sweeps per launch, prolongation with residual
             // update) on smoothed depths of shared operators
+            const bool stage = so.halo_fusion == 3;
             if (!P->pc && so.precond == MG_PRECOND_MULTIGRID && d + 1 < nd && so.halo_fusion != 1 &&
-                smooth2_shape(D.n, mm.ell_bw, ntile, c->sm_count > 0 ? c->sm_count : 1, D.f_cw, D.f_R)) {
+                smooth2_shape(D.n, mm.ell_bw, ntile, c->sm_count > 0 ? c->sm_count : 1, stage, D.f_cw, D.f_R)) {
                 D.f_H = mm.ell_bw;
                 D.f_nrb = (D.n + D.f_R - 1) / D.f_R;
-                smooth2_allow_smem<8, true>();
-                smooth2_allow_smem<8, false>();
-                smooth2_allow_smem<16, true>();
-                smooth2_allow_smem<16, false>();
+                D.f_stage = stage;
+                smooth2_allow_smem<8, true, false>();
+                smooth2_allow_smem<8, false, false>();
+                smooth2_allow_smem<16, true, false>();
+                smooth2_allow_smem<16, false, false>();
+                smooth2_allow_smem<8, true, true>();
+                smooth2_allow_smem<8, false, true>();
+                smooth2_allow_smem<16, true, true>();
+                smooth2_allow_smem<16, false, true>();
                 MG_CUDA(cudaFuncSetAttribute(kb_prolong_res<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)SMOOTH2_SMEM_MAX));
                 MG_CUDA(cudaFuncSetAttribute(kb_prolong_res<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -484,7 +484,7 @@ void check_solver_opts(const mg_solver_opts& so) {
         !(so.base_tiles == 0 || so.base_tiles == 1 || so.base_tiles == 2 || so.base_tiles == 4) ||
         (so.smoother != MG_SMOOTH_CHEBYSHEV && so.smoother != MG_SMOOTH_JACOBI) ||
         !(so.cheb_ratio == 0.0 || (so.cheb_ratio > 1.0 && so.cheb_ratio <= 1e4)) || so.halo_fusion < 0 ||
-        so.halo_fusion > 2 || so.base_cores < 0 || so.base_cores > 2)
+        so.halo_fusion > 3 || so.base_cores < 0 || so.base_cores > 2)
         mg_fail(MG_EINVAL, "bad solver options");
 }
 

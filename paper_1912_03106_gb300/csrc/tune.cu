@@ -130,7 +130,7 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
                     const double ms = time_of(t);
                     if (ms < gt) gt = ms, gb = t;
                 }
-                for (int hf : {1, 2}) {
+                for (int hf : {1, 2, 3}) {
                     Trial t = gb;
                     t.hf = hf;
                     const double ms = time_of(t);

@@ -4,9 +4,10 @@ cores of the dense base solve.
 With `halo_fusion` 2 the V-cycle runs two consecutive smoothing sweeps per launch
 (the first sweep's residual formed in shared memory on a halo of the operator's
 bandwidth, the second gathered from there) and the prolongation together with the
-residual update (the prolongated correction likewise kept in shared memory).  The
-kernels do the arithmetic of the single-phase kernels in the same order, so a
-batched step with `halo_fusion` 2 must give the step with 1: the same PCG
+residual update (the prolongated correction likewise kept in shared memory); with 3
+the sweeps' input is staged in shared memory as well.  The kernels do the
+arithmetic of the single-phase kernels in the same order, so a batched step with
+`halo_fusion` 2 or 3 must give the step with 1: the same PCG
 iteration counts and the same result (to rounding), and both the oracle's exact
 step solve (banded Cholesky of L = M/dt + K) to the bar of the other FP64 step
 tests.  Cases: several 16-column tiles with a ragged last one, 8- and 16-column
@@ -66,15 +67,16 @@ def test_halo_fused_kernels_give_the_same_step(setup, level, k, precision, smoot
     x = torch.as_tensor(xn, device="cuda")
     out = {}
     its = {}
-    for hf in (1, 2):
+    for hf in (1, 2, 3):
         so = api.solver_opts(path=2, precision=precision, smooth=smooth, halo_fusion=hf)
         y = torch.zeros_like(x)
         _, st = ctx.mg_step(ids[level], N, T, x, y, i0=1, istride=1, solver=so)
         out[hf], its[hf] = y, st["cg_iters"]
-    assert abs(its[1] - its[2]) <= k // 16, its
-    diff = ((out[2] - out[1]).norm(dim=0) / out[1].norm(dim=0)).max().item()
-    assert diff <= 1e-11, diff
-    g = out[2].cpu().numpy()
+    for hf in (2, 3):
+        assert abs(its[1] - its[hf]) <= k // 16, its
+        diff = ((out[hf] - out[1]).norm(dim=0) / out[1].norm(dim=0)).max().item()
+        assert diff <= 1e-11, (hf, diff)
+    g = out[3].cpu().numpy()
     for c in sorted({0, k // 2, k - 1}):
         want = oracle_step(meshes, model, level, xn[:, c], 1 + c)
         assert np.linalg.norm(g[:, c] - want) <= 1e-10 * np.linalg.norm(want), c
@@ -86,7 +88,7 @@ def test_halo_fusion_is_validated(setup):
     x = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
     y = torch.zeros_like(x)
     with pytest.raises(api.L.MgError) as e:
-        ctx.mg_step(ids[0], N, T, x, y, solver=api.solver_opts(halo_fusion=3))
+        ctx.mg_step(ids[0], N, T, x, y, solver=api.solver_opts(halo_fusion=4))
     assert e.value.status == -1
 
 
