@@ -95,6 +95,7 @@ struct Depth {
     const double* L64;
     const double* M64;
     const float* L32;
+    const float* Llo32;  // shared operators: L64 - L32 in FP32 (double-float operator products)
     const float* LD32;
     const float* dinv32;
     const int32_t* par;  // transfer to the next coarser depth
@@ -1391,11 +1392,80 @@ template <class T, bool PC>
 __host__ __device__ constexpr int minb_a() {
     return PC ? (std::is_same<T, double>::value ? 3 : 2) : MG_MINB_A;
 }
-template <class T, bool PC>
+
+// Double-float operator product acc[e] = sum_w L[w, i] z[col[w, i]][c0 + e] for an
+// FP64 operator given as L = Lh + Ll (two FP32 arrays) and an FP32 vector z, in
+// FP32 arithmetic: each Lh z is formed exactly as a rounded product and its FMA
+// error term, the rounded products are summed by two-sum (the rounding error of
+// every addition is kept), the error terms and the Ll z products are summed in
+// FP32, and the two sums are widened and added once in FP64.  The result carries
+// about 2^-46 of sum_j |L_ij z_j| (FP64 arithmetic: about 2^-50); it replaces 7
+// FP64 FMAs per row by about 70 FP32 operations and one FP64 addition, which on
+// GB300 (FP32 rate many times the FP64 rate) is the cheaper way to FP64-class
+// products.
+template <int V>
+__device__ __forceinline__ void ell_vec_df(const int32_t* __restrict__ col, const float* __restrict__ Lh,
+                                           const float* __restrict__ Ll, int n, int W, int i, const float* z, int c0,
+                                           double (&acc)[V]) {
+    float hi[V], lo[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) hi[e] = lo[e] = 0.0f;
+    auto add = [&](float ah, float al, const float (&zv)[V]) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const float p = __fmul_rn(ah, zv[e]);
+            const float pe = __fmaf_rn(ah, zv[e], -p);  // ah * z = p + pe exactly
+            const float s = __fadd_rn(hi[e], p);
+            const float bp = __fsub_rn(s, hi[e]);
+            const float err = __fadd_rn(__fsub_rn(hi[e], __fsub_rn(s, bp)), __fsub_rn(p, bp));  // hi + p = s + err
+            hi[e] = s;
+            lo[e] = __fmaf_rn(al, zv[e], __fadd_rn(lo[e], __fadd_rn(err, pe)));
+        }
+    };
+    int32_t j[WMAX];
+    float ah[WMAX], al[WMAX];
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < W) {
+            j[w] = __ldg(col + w * n + i);
+            ah[w] = __ldg(Lh + w * n + i);
+            al[w] = __ldg(Ll + w * n + i);
+        }
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < W) {
+            float zv[V];
+            vld<float, V>(z + j[w] * G + c0, zv);
+            add(ah[w], al[w], zv);
+        }
+    for (int w = WMAX; w < W; ++w) {
+        float zv[V];
+        vld<float, V>(z + __ldg(col + w * n + i) * G + c0, zv);
+        add(__ldg(Lh + w * n + i), __ldg(Ll + w * n + i), zv);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) acc[e] = f2d_int(hi[e]) + f2d_int(lo[e]);
+}
+
+// The double-float product serves steps whose tolerance leaves room for its
+// accuracy: cg_tol >= 1e-8 (its residual drift stays below 1e-3 of the tolerance).
+// The FP64 form launches both variants of kb_pcg_a; the one whose mode this call's
+// tolerance does not select returns at once (each keeps its own register budget).
+constexpr double kDfTol2 = 1e-16;
+__device__ __forceinline__ bool use_df(const Depth& D, const CallArgs* ca) {
+    return D.Llo32 && ca->tol2 >= kDfTol2;
+}
+
+template <class T, bool PC, bool DF = false>
 __global__ void __launch_bounds__(NTB, minb_a<T, PC>()) kb_pcg_a(Depth D, const T* Lv, T* p_base, T* q_base, const double* beta,
-                                                double* part) {
+                                                double* part, const CallArgs* __restrict__ ca) {
+    static_assert(!DF || (std::is_same<T, double>::value && !PC), "double-float products: FP64 form, shared operator");
     phase_begin();
     constexpr int V = VecOf<T>::V, TPR = G / V, RPP = NTB / TPR;
+    constexpr bool kDf = std::is_same<T, double>::value && !PC;
+    if constexpr (kDf) {
+        if (use_df(D, ca) != DF) return;  // the other variant runs this call
+    }
     int t, rb;
     tile_rb(D.nrb, t, rb);
     if (!tile_on(D.tact, t)) return;
@@ -1411,7 +1481,8 @@ __global__ void __launch_bounds__(NTB, minb_a<T, PC>()) kb_pcg_a(Depth D, const 
     for (int i = rb * D.rbs + threadIdx.x / TPR; i < i1; i += RPP) {
         T lz[V], pv[V], qv[V];
         float zv[V];
-        ell_vec_w<V, T, T, float, PC>(D.col, tile_vals<PC>(Lv, D, t), D.n, D.W, i, z, c0, lz);
+        if constexpr (DF) ell_vec_df<V>(D.col, D.L32, D.Llo32, D.n, D.W, i, z, c0, lz);
+        else ell_vec_w<V, T, T, float, PC>(D.col, tile_vals<PC>(Lv, D, t), D.n, D.W, i, z, c0, lz);
         vld<float, V>(z + i * G + c0, zv);
         vld<T, V>(p + i * G + c0, pv);
         vld<T, V>(q + i * G + c0, qv);
@@ -1749,8 +1820,15 @@ void capture_pcg_body(GraphPlan& P, cudaStream_t s, T* d, T* r, T* p, T* q, cons
     else rf = r;
     capture_precondition<float>(P, s, rf, part);
     pdl_launch(kb_scalar_gamma, P.ntile, NTB, 0, s, P.st, part, D0.nrb);
-    if (P.pc) pdl_launch(kb_pcg_a<T, true>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, Lv, p, q, P.st.beta, part);
-    else pdl_launch(kb_pcg_a<T, false>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, Lv, p, q, P.st.beta, part);
+    if (P.pc) {
+        pdl_launch(kb_pcg_a<T, true>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, Lv, p, q, P.st.beta, part, ca);
+    } else {
+        pdl_launch(kb_pcg_a<T, false>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, Lv, p, q, P.st.beta, part, ca);
+        if constexpr (std::is_same<T, double>::value)
+            if (D0.Llo32)
+                pdl_launch(kb_pcg_a<T, false, true>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, Lv, p, q, P.st.beta, part,
+                           ca);
+    }
     pdl_launch(kb_scalar_alpha, P.ntile, NTB, 0, s, P.st, part, D0.nrb);
     pdl_launch(kb_pcg_b<T>, grid(P.ntile, D0.nrb), NTB, 0, s, D0, d, r, p, q, P.st.alpha, part,
                                                        std::is_same<T, double>::value ? P.r32s : nullptr);
@@ -1866,12 +1944,14 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             D.L64 = md.L64.as<double>();
             D.M64 = md.M64.as<double>();
             D.L32 = md.L32.as<float>();
+            D.Llo32 = md.Llo32.as<float>();
             D.LD32 = md.LD32.as<float>();
             D.dinv32 = md.dinv32.as<float>();
             if (P->pc) {  // per-column Jacobians replace the step operator's values
                 D.L64 = pco->d[d].J64;
                 D.M64 = nullptr;
                 D.L32 = pco->d[d].J32;
+                D.Llo32 = nullptr;
                 D.LD32 = pco->d[d].LD32;
                 D.dinv32 = pco->d[d].dinv32;
             }

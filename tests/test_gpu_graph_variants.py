@@ -17,6 +17,10 @@ odd and even sweep counts (pairs only, or pairs and single sweeps).
 The dense base solve x = A^-1 r runs on the CUDA cores (FP32 FMA) or on the
 tensor cores (3xTF32 mma.sync); both are FP32-accurate preconditioner pieces,
 so both steps meet the oracle's bar; 1, 2 and 4 tiles per block, ragged tiles.
+
+Steps of the FP64 form with cg_tol >= 1e-8 form the operator products of the
+Krylov update in double-float FP32 arithmetic; their true residual, computed on the
+CPU with the oracle's matrices, must meet the requested tolerance.
 """
 
 import numpy as np
@@ -110,3 +114,25 @@ def test_base_solve_on_cuda_and_tensor_cores(setup, level, k, tiles):
         for bc in (1, 2):
             got = out[bc][:, c].cpu().numpy()
             assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want), (bc, c)
+
+
+@pytest.mark.parametrize("level,k,tol", [(2, 256, 1e-8), (2, 40, 1e-6), (1, 64, 3e-5)])
+def test_double_float_products_meet_the_tolerance(setup, level, k, tol):
+    """Per column ||b - L x|| <= 1.01 tol ||b|| with b = (M/dt) x_prev + f(t_i) and
+    L = M/dt + K from the oracle's FE matrices, and the step agrees with the
+    oracle's exact solve to the accuracy the tolerance allows."""
+    meshes, model, ctx, ids = setup
+    n = ctx.mg_num_dofs(ids[level])
+    xn = 0.01 * np.random.default_rng(500 + k).standard_normal((n, k))
+    x = torch.as_tensor(xn, device="cuda")
+    y = torch.zeros_like(x)
+    _, st = ctx.mg_step(ids[level], N, T, x, y, i0=1, istride=1, solver=api.solver_opts(path=2, cg_tol=tol))
+    assert st["worst_status"] in (0, "MG_OK"), st
+    fe = fem.FEModel(meshes[level], model)
+    forcing = stepper.Forcing(fe.F, model.pwm.J0, opwm.sign_table(model.pwm, T, N), 1)
+    phi = stepper.LinearPhi(fe, T / N, forcing)
+    g = y.cpu().numpy()
+    for c in sorted({0, 1, k // 2, k - 1}):
+        b = phi.Mdt @ xn[:, c] + forcing(1 + c)
+        r = b - phi.L @ g[:, c]
+        assert np.linalg.norm(r) <= 1.01 * tol * np.linalg.norm(b), (c, np.linalg.norm(r) / np.linalg.norm(b))
