@@ -167,6 +167,20 @@ __device__ __forceinline__ double col_total(const double* part, int nrb, int gc)
 template <class T>
 __device__ __forceinline__ T* tv(T* base, int n, int t) { return base + (size_t)t * n * G; }
 
+// Double-float operator products (DfAcc) serve the FP64 form's steps whose
+// tolerance leaves room for their accuracy (about 2^-46 of sum |L_ij z_j| against
+// FP64's 2^-50): cg_tol >= 1e-8, where the resulting drift of the recursive
+// residual stays orders of magnitude below the stop test.  The FP64 form launches
+// both variants of kb_pcg_a; the one that this call's tolerance (read on the
+// device) does not select returns at once, and each keeps its own register budget.
+// (kb_init keeps FP64 products: both of its operands are FP64, and splitting each
+// gathered value into two floats by integer instructions measured slower, 246
+// against 218 us at 18,240 x 256, than the FP64 pipe.)
+constexpr double kDfTol2 = 1e-16;
+__device__ __forceinline__ bool use_df(const Depth& D, const CallArgs* ca) {
+    return D.Llo32 && ca->tol2 >= kDfTol2;
+}
+
 // ---------------------------------------------------------------- set-up and final phases
 // b = (1/dt) M x_prev + J0 sum_s b_s F_s, x0 = guess - g; FP64 form: r = b - L x0;
 // FP32+refinement: b kept, the FP32 correction and Krylov vectors d, p, q zeroed.
@@ -504,22 +518,6 @@ __global__ void __launch_bounds__(NSB) kb_scalar_final(Cols st, int kpad, const 
         else if (failed) atomicMin(worst, (int)MG_ECG_MAXIT);
         atomicAdd(iter_sum, (unsigned long long)st.iters[c]);
     }
-}
-
-// Exact float -> double conversion with integer instructions: on GB300 the F2F
-// conversion issues on the FP64 pipe, whose rate is a small fraction of FP32's.
-// Normal numbers and zeros convert by moving bits; infinities stay infinities and
-// NaNs stay NaNs (exponent all ones maps to all ones, the mantissa bits are kept),
-// so a poisoned preconditioner output reaches the convergence test instead of
-// turning into a large finite number; the rare denormals take the hardware path.
-__device__ __forceinline__ double f2d_int(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u && (u & 0x7fffffu)) return (double)f;
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    const unsigned long long mant = (unsigned long long)(u & 0x7fffffu) << 29;
-    const unsigned long long ex = (unsigned long long)(e == 0xffu ? 0x7ffu : e + (1023u - 127u)) << 52;
-    return __longlong_as_double((long long)(e ? (sign | ex | mant) : sign));
 }
 
 template <class A, class X>
@@ -1144,12 +1142,17 @@ __global__ void __launch_bounds__(128) kb_base_dense(int n0, const float* __rest
 // partial outputs as kb_base_dense).  A thread owns 4 rows x CT columns of the
 // block's 64 x TB*16 outputs; the A slice is staged transposed so that a thread
 // reads its 4 rows of one k as one float4, the r slice row-major so that it reads
-// its CT columns as float4s.
+// its CT columns as float4s.  When the base size is a multiple of 4 the slices
+// are fetched as float4s into registers one step ahead, so that their global
+// latency overlaps the previous step's arithmetic; otherwise element by element.
 template <class RT, int TB, int BKT>
 __global__ void __launch_bounds__(128) kb_base_cc(int n0, const float* __restrict__ A, const RT* r_base, float* x_base,
                                                   int ntile, int ks, size_t pstride) {
-    constexpr int NC = TB * G;        // columns per block
-    constexpr int CT = NC / 8;        // columns per thread (8 column groups)
+    constexpr int NC = TB * G;                 // columns per block
+    constexpr int CT = NC / 8;                 // columns per thread (8 column groups)
+    constexpr int AQ = 64 * BKT / 4 / 128;     // float4s of the A slice per thread
+    constexpr int BQ = BKT * NC / 4 / 128;     // float4s of the r slice per thread
+    static_assert(AQ >= 1 && BQ >= 1 && BKT % 4 == 0, "slice shape");
     phase_begin();
     __shared__ __align__(16) float At[BKT][64 + 4];
     __shared__ __align__(16) float Bs[BKT][NC];
@@ -1161,18 +1164,7 @@ __global__ void __launch_bounds__(128) kb_base_cc(int n0, const float* __restric
     x_base += (size_t)split * pstride;
     const int r0 = (threadIdx.x / 8) * 4, c0 = (threadIdx.x % 8) * CT;
     float acc[4][CT] = {};
-    for (int k0 = kbeg; k0 < kend; k0 += BKT) {
-        for (int q = threadIdx.x; q < 64 * BKT; q += 128) {
-            const int rr = q / BKT, kk = q % BKT;
-            const int gi = ib * 64 + rr, gk = k0 + kk;
-            At[kk][rr] = (gi < n0 && gk < kend) ? __ldg(A + (size_t)gi * n0 + gk) : 0.0f;
-        }
-        for (int q = threadIdx.x; q < BKT * NC; q += 128) {
-            const int kk = q / NC, cc = q % NC;
-            const int t = cg * TB + cc / G, gk = k0 + kk;
-            Bs[kk][cc] = (gk < kend && t < ntile) ? (float)r_base[((size_t)t * n0 + gk) * G + cc % G] : 0.0f;
-        }
-        __syncthreads();
+    auto compute = [&]() {
 #pragma unroll 4
         for (int kk = 0; kk < BKT; ++kk) {
             const float4 a = *reinterpret_cast<const float4*>(&At[kk][r0]);
@@ -1202,7 +1194,65 @@ __global__ void __launch_bounds__(128) kb_base_cc(int n0, const float* __restric
                 acc[3][c] += a.w * b[c];
             }
         }
-        __syncthreads();
+    };
+    if (std::is_same<RT, float>::value && (n0 & 3) == 0) {
+        // k ranges start at multiples of BKT and end at n0 or such a multiple: a
+        // float4 of A or r lies wholly inside or wholly outside [kbeg, kend)
+        float4 ra[AQ], rv[BQ];
+        auto load = [&](int k0) {
+#pragma unroll
+            for (int u = 0; u < AQ; ++u) {
+                const int q = threadIdx.x + u * 128;
+                const int rr = q / (BKT / 4), gk = k0 + 4 * (q % (BKT / 4)), gi = ib * 64 + rr;
+                ra[u] = (gi < n0 && gk < kend) ? __ldg(reinterpret_cast<const float4*>(A + (size_t)gi * n0 + gk))
+                                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < BQ; ++u) {
+                const int q = threadIdx.x + u * 128;
+                const int gk = k0 + q / (NC / 4), cc = 4 * (q % (NC / 4)), t = cg * TB + cc / G;
+                rv[u] = (gk < kend && t < ntile)
+                            ? *reinterpret_cast<const float4*>(r_base + ((size_t)t * n0 + gk) * G + cc % G)
+                            : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        };
+        load(kbeg);
+        for (int k0 = kbeg; k0 < kend; k0 += BKT) {
+#pragma unroll
+            for (int u = 0; u < AQ; ++u) {
+                const int q = threadIdx.x + u * 128;
+                const int rr = q / (BKT / 4), k4 = 4 * (q % (BKT / 4));
+                At[k4][rr] = ra[u].x;
+                At[k4 + 1][rr] = ra[u].y;
+                At[k4 + 2][rr] = ra[u].z;
+                At[k4 + 3][rr] = ra[u].w;
+            }
+#pragma unroll
+            for (int u = 0; u < BQ; ++u) {
+                const int q = threadIdx.x + u * 128;
+                *reinterpret_cast<float4*>(&Bs[q / (NC / 4)][4 * (q % (NC / 4))]) = rv[u];
+            }
+            __syncthreads();
+            if (k0 + BKT < kend) load(k0 + BKT);
+            compute();
+            __syncthreads();
+        }
+    } else {
+        for (int k0 = kbeg; k0 < kend; k0 += BKT) {
+            for (int q = threadIdx.x; q < 64 * BKT; q += 128) {
+                const int rr = q / BKT, kk = q % BKT;
+                const int gi = ib * 64 + rr, gk = k0 + kk;
+                At[kk][rr] = (gi < n0 && gk < kend) ? __ldg(A + (size_t)gi * n0 + gk) : 0.0f;
+            }
+            for (int q = threadIdx.x; q < BKT * NC; q += 128) {
+                const int kk = q / NC, cc = q % NC;
+                const int t = cg * TB + cc / G, gk = k0 + kk;
+                Bs[kk][cc] = (gk < kend && t < ntile) ? (float)r_base[((size_t)t * n0 + gk) * G + cc % G] : 0.0f;
+            }
+            __syncthreads();
+            compute();
+            __syncthreads();
+        }
     }
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
@@ -1407,20 +1457,10 @@ template <int V>
 __device__ __forceinline__ void ell_vec_df(const int32_t* __restrict__ col, const float* __restrict__ Lh,
                                            const float* __restrict__ Ll, int n, int W, int i, const float* z, int c0,
                                            double (&acc)[V]) {
-    float hi[V], lo[V];
-#pragma unroll
-    for (int e = 0; e < V; ++e) hi[e] = lo[e] = 0.0f;
+    DfAcc d[V];
     auto add = [&](float ah, float al, const float (&zv)[V]) {
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const float p = __fmul_rn(ah, zv[e]);
-            const float pe = __fmaf_rn(ah, zv[e], -p);  // ah * z = p + pe exactly
-            const float s = __fadd_rn(hi[e], p);
-            const float bp = __fsub_rn(s, hi[e]);
-            const float err = __fadd_rn(__fsub_rn(hi[e], __fsub_rn(s, bp)), __fsub_rn(p, bp));  // hi + p = s + err
-            hi[e] = s;
-            lo[e] = __fmaf_rn(al, zv[e], __fadd_rn(lo[e], __fadd_rn(err, pe)));
-        }
+        for (int e = 0; e < V; ++e) d[e].add(ah, al, zv[e]);
     };
     int32_t j[WMAX];
     float ah[WMAX], al[WMAX];
@@ -1444,16 +1484,7 @@ __device__ __forceinline__ void ell_vec_df(const int32_t* __restrict__ col, cons
         add(__ldg(Lh + w * n + i), __ldg(Ll + w * n + i), zv);
     }
 #pragma unroll
-    for (int e = 0; e < V; ++e) acc[e] = f2d_int(hi[e]) + f2d_int(lo[e]);
-}
-
-// The double-float product serves steps whose tolerance leaves room for its
-// accuracy: cg_tol >= 1e-8 (its residual drift stays below 1e-3 of the tolerance).
-// The FP64 form launches both variants of kb_pcg_a; the one whose mode this call's
-// tolerance does not select returns at once (each keeps its own register budget).
-constexpr double kDfTol2 = 1e-16;
-__device__ __forceinline__ bool use_df(const Depth& D, const CallArgs* ca) {
-    return D.Llo32 && ca->tol2 >= kDfTol2;
+    for (int e = 0; e < V; ++e) acc[e] = d[e].value();
 }
 
 template <class T, bool PC, bool DF = false>

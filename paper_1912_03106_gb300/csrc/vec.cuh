@@ -118,4 +118,39 @@ __device__ __forceinline__ float abs_to_float(double x) {
     return __uint_as_float(((unsigned)e << 23) | (unsigned)((u >> 29) & 0x7fffffull));
 }
 
+// Exact float -> double conversion with integer instructions: on GB300 the F2F
+// conversion issues on the FP64 pipe, whose rate is a small fraction of FP32's.
+// Normal numbers and zeros convert by moving bits; infinities stay infinities and
+// NaNs stay NaNs (exponent all ones maps to all ones, the mantissa bits are kept),
+// so a poisoned preconditioner output reaches the convergence test instead of
+// turning into a large finite number; the rare denormals take the hardware path.
+__device__ __forceinline__ double f2d_int(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u && (u & 0x7fffffu)) return (double)f;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long mant = (unsigned long long)(u & 0x7fffffu) << 29;
+    const unsigned long long ex = (unsigned long long)(e == 0xffu ? 0x7ffu : e + (1023u - 127u)) << 52;
+    return __longlong_as_double((long long)(e ? (sign | ex | mant) : sign));
+}
+
+// Double-float accumulator of products in FP32 arithmetic: hi holds the running
+// sum of the rounded leading products (each addition's rounding error is kept by
+// two-sum), lo the FP32 sum of those errors, of the products' own FMA error terms
+// and of the small products al * z; value() widens both and adds them once in FP64.
+struct DfAcc {
+    float hi = 0.0f, lo = 0.0f;
+    // += (ah + al) z
+    __device__ __forceinline__ void add(float ah, float al, float z) {
+        const float p = __fmul_rn(ah, z);
+        const float pe = __fmaf_rn(ah, z, -p);  // ah * z = p + pe exactly
+        const float s = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));  // hi + p = s + err
+        hi = s;
+        lo = __fmaf_rn(al, z, __fadd_rn(lo, __fadd_rn(err, pe)));
+    }
+    __device__ __forceinline__ double value() const { return f2d_int(hi) + f2d_int(lo); }
+};
+
 }  // namespace mgv
