@@ -96,6 +96,7 @@ struct Depth {
     const double* M64;
     const float* L32;
     const float* Llo32;  // shared operators: L64 - L32 in FP32 (double-float operator products)
+    const float *M32, *Mlo32;  // shared operators: M64 as two FP32 parts
     const float* LD32;
     const float* dinv32;
     const int32_t* par;  // transfer to the next coarser depth
@@ -173,24 +174,87 @@ __device__ __forceinline__ T* tv(T* base, int n, int t) { return base + (size_t)
 // residual stays orders of magnitude below the stop test.  The FP64 form launches
 // both variants of kb_pcg_a; the one that this call's tolerance (read on the
 // device) does not select returns at once, and each keeps its own register budget.
-// (kb_init keeps FP64 products: both of its operands are FP64, and splitting each
-// gathered value into two floats by integer instructions measured slower, 246
-// against 218 us at 18,240 x 256, than the FP64 pipe.)
+// kb_init's products have FP64 operands on both sides: kb_split first writes
+// x_prev and the guess as two FP32 parts each, once per step (splitting each value
+// at every one of its ~7 gathers measured slower than the FP64 pipe: 246 against
+// 218 us at 18,240 x 256), and kb_init's double-float variant gathers those parts.
 constexpr double kDfTol2 = 1e-16;
 __device__ __forceinline__ bool use_df(const Depth& D, const CallArgs* ca) {
     return D.Llo32 && ca->tol2 >= kDfTol2;
+}
+__device__ __forceinline__ bool use_df_init(const Depth& D, const CallArgs* ca) {
+    return use_df(D, ca) && D.M32 && !ca->g;
+}
+
+// x_prev and the guess (FP64, the caller's layout) as two FP32 parts each,
+// tile-major, for kb_init's double-float variant; returns at once when that
+// variant does not run this call.  The guess parts are zero without a guess.
+__global__ void __launch_bounds__(NTB) kb_split(Depth D, const CallArgs* __restrict__ ca, float* ph, float* pl,
+                                                float* gh, float* gl) {
+    phase_begin();
+    if (!use_df_init(D, ca)) return;
+    int t, rb;
+    tile_rb(D.nrb, t, rb);
+    const int lc = threadIdx.x % G, gc = t * G + lc;
+    const bool valid = gc < ca->k;
+    const int i1 = min(D.n, (rb + 1) * D.rbs);
+    for (int i = rb * D.rbs + threadIdx.x / G; i < i1; i += NTB / G) {
+        float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f;
+        if (valid) {
+            split_d2f(ca->xprev[(int64_t)i * ca->ld_prev + gc], a, b);
+            if (ca->guess) split_d2f(ca->guess[(int64_t)i * ca->ld_guess + gc], c, d);
+        }
+        const size_t o = ((size_t)t * D.n + i) * G + lc;
+        ph[o] = a;
+        pl[o] = b;
+        gh[o] = c;
+        gl[o] = d;
+    }
+}
+
+// sum_w (Ah + Al)[w, i] (xh + xl)[col[w, i]] over tile-major split parts, column lc
+__device__ __forceinline__ double ell_df_split(const Depth& D, const float* Ah, const float* Al, const float* xh,
+                                               const float* xl, int i, int lc, float* absum) {
+    DfAcc acc;
+    int j[WMAX];
+    float ah[WMAX], al[WMAX];
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < D.W) {
+            j[w] = __ldg(D.col + w * D.n + i);
+            ah[w] = __ldg(Ah + w * D.n + i);
+            al[w] = __ldg(Al + w * D.n + i);
+        }
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w)
+        if (w < D.W) {
+            const float h = xh[j[w] * G + lc], l = xl[j[w] * G + lc];
+            acc.add(ah[w], al[w], h, l);
+            if (absum) *absum += fabsf(ah[w]) * fabsf(h);
+        }
+    for (int w = WMAX; w < D.W; ++w) {
+        const int jw = __ldg(D.col + w * D.n + i);
+        const float aw = __ldg(Ah + w * D.n + i), h = xh[jw * G + lc];
+        acc.add(aw, __ldg(Al + w * D.n + i), h, xl[jw * G + lc]);
+        if (absum) *absum += fabsf(aw) * fabsf(h);
+    }
+    return acc.value();
 }
 
 // ---------------------------------------------------------------- set-up and final phases
 // b = (1/dt) M x_prev + J0 sum_s b_s F_s, x0 = guess - g; FP64 form: r = b - L x0;
 // FP32+refinement: b kept, the FP32 correction and Krylov vectors d, p, q zeroed.
-template <int MODE>
-__global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restrict__ ca, double inv_dt,
+// DF (FP64 form): M x_prev and L x0 as double-float products over the FP32 parts
+// kb_split wrote (sp: x_prev high, low, guess high, low, each tile-major).
+template <int MODE, bool DF = false>
+__global__ void __launch_bounds__(NTB, DF ? 2 : 4) kb_init(Depth D, const CallArgs* __restrict__ ca, double inv_dt,
                                                const double* __restrict__ F, double J0, double* x64, double* r64,
                                                double* p64, double* q64, double* b64, float* z, double* part_bb,
                                                double* part_rr, double* part_ss, float* r32s, float* d32, float* p32,
-                                               float* q32) {
+                                               float* q32, const float* __restrict__ sp = nullptr) {
+    static_assert(!DF || MODE == 0, "double-float products: FP64 form");
     phase_begin();
+    if (MODE == 0 && sp && use_df_init(D, ca) != DF) return;  // the other variant runs this call
     int t, rb;
     tile_rb(D.nrb, t, rb);
     const int lc = threadIdx.x % G, gc = t * G + lc;
@@ -210,14 +274,22 @@ __global__ void __launch_bounds__(NTB) kb_init(Depth D, const CallArgs* __restri
         float alx = 0.0f;  // sum |L_ij| |x_j| of the rounding floor (an estimate: FP32)
         if (valid) {
             double mb = 0.0;
-            for (int w = 0; w < D.W; ++w) {
-                const int64_t j = __ldg(D.col + w * D.n + i);
-                mb += __ldg(D.M64 + w * D.n + i) * xprev[j * ca->ld_prev + gc];
-                if (guess) {
-                    double xj = guess[j * ca->ld_guess + gc];
-                    if (g) xj -= g[j * ca->ld_g + gc];
-                    lx += __ldg(D.L64 + w * D.n + i) * xj;
-                    alx += fabsf(__ldg(D.L32 + w * D.n + i)) * abs_to_float(xj);
+            if constexpr (DF) {  // g is null here (use_df_init)
+                const size_t e = (size_t)D.n * G, tb = (size_t)t * e;
+                mb = ell_df_split(D, D.M32, D.Mlo32, sp + tb, sp + e * gridDim.x / D.nrb + tb, i, lc, nullptr);
+                if (guess)
+                    lx = ell_df_split(D, D.L32, D.Llo32, sp + 2 * e * (gridDim.x / D.nrb) + tb,
+                                      sp + 3 * e * (gridDim.x / D.nrb) + tb, i, lc, &alx);
+            } else {
+                for (int w = 0; w < D.W; ++w) {
+                    const int64_t j = __ldg(D.col + w * D.n + i);
+                    mb += __ldg(D.M64 + w * D.n + i) * xprev[j * ca->ld_prev + gc];
+                    if (guess) {
+                        double xj = guess[j * ca->ld_guess + gc];
+                        if (g) xj -= g[j * ca->ld_g + gc];
+                        lx += __ldg(D.L64 + w * D.n + i) * xj;
+                        alx += fabsf(__ldg(D.L32 + w * D.n + i)) * abs_to_float(xj);
+                    }
                 }
             }
             bi = mb * inv_dt + J0 * (sg[0] * F[i] + sg[1] * F[D.n + i] + sg[2] * F[2 * D.n + i]);
@@ -1665,6 +1737,7 @@ struct GraphPlan {
     double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *b64 = nullptr;
     float *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     float* r32s = nullptr;  // FP64 form: FP32 shadow of the residual
+    float* split = nullptr; // FP64 form, shared operator: x_prev and guess as FP32 parts (kb_split)
     ~GraphPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -1933,6 +2006,22 @@ void smooth2_allow_smem() {
                                  (int)SMOOTH2_SMEM_MAX));
 }
 
+// The FP64 form's set-up phase: with split buffers, kb_split and both variants of
+// kb_init (the one this call's tolerance selects runs, the others return at once).
+void launch_init0(GraphPlan& P, cudaStream_t s, const CallArgs* ca, double inv_dt, const double* F, double J0,
+                  double* part, double* part2, double* part3) {
+    Depth& D0 = P.depth[0];
+    const unsigned g = grid(P.ntile, D0.nrb);
+    const size_t e0 = (size_t)P.ntile * D0.n * G;
+    float* sp = P.split;
+    if (sp && D0.M32) kb_split<<<g, NTB, 0, s>>>(D0, ca, sp, sp + e0, sp + 2 * e0, sp + 3 * e0);
+    kb_init<0><<<g, NTB, 0, s>>>(D0, ca, inv_dt, F, J0, P.x64, P.r64, P.p64, P.q64, nullptr, D0.x, part, part2, part3,
+                                 P.r32s, nullptr, nullptr, nullptr, sp && D0.M32 ? sp : nullptr);
+    if (sp && D0.M32)
+        kb_init<0, true><<<g, NTB, 0, s>>>(D0, ca, inv_dt, F, J0, P.x64, P.r64, P.p64, P.q64, nullptr, D0.x, part,
+                                           part2, part3, P.r32s, nullptr, nullptr, nullptr, sp);
+}
+
 GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_opts& so,
                       const PcOperator* pco = nullptr) {
     auto* P = new GraphPlan();
@@ -1976,6 +2065,8 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             D.M64 = md.M64.as<double>();
             D.L32 = md.L32.as<float>();
             D.Llo32 = md.Llo32.as<float>();
+            D.M32 = md.M32.as<float>();
+            D.Mlo32 = md.Mlo32.as<float>();
             D.LD32 = md.LD32.as<float>();
             D.dinv32 = md.dinv32.as<float>();
             if (P->pc) {  // per-column Jacobians replace the step operator's values
@@ -1983,6 +2074,7 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
                 D.M64 = nullptr;
                 D.L32 = pco->d[d].J32;
                 D.Llo32 = nullptr;
+                D.M32 = D.Mlo32 = nullptr;
                 D.LD32 = pco->d[d].LD32;
                 D.dinv32 = pco->d[d].dinv32;
             }
@@ -2033,6 +2125,7 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
             P->p64 = (double*)alloc(*P, e0 * 8);
             P->q64 = (double*)alloc(*P, e0 * 8);
             P->r32s = (float*)alloc(*P, e0 * 4);
+            if (!P->pc) P->split = (float*)alloc(*P, e0 * 4 * 4);
         } else {
             P->b64 = (double*)alloc(*P, e0 * 8);
             P->d32 = (float*)alloc(*P, e0 * 4);
@@ -2083,9 +2176,7 @@ GraphPlan* build_plan(mg_ctx* c, const StepOp& op, int ntile, const mg_solver_op
                 kb_init_pc<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, pco->R, pco->state, P->x64, P->r64, P->p64, P->q64,
                                                              D0.x, part, part2, P->r32s);
             else
-                kb_init<0><<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, inv_dt, m0.F.as<double>(), J0, P->x64, P->r64,
-                                                             P->p64, P->q64, nullptr, D0.x, part, part2, part3,
-                                                             P->r32s, nullptr, nullptr, nullptr);
+                launch_init0(*P, s, ca, inv_dt, m0.F.as<double>(), J0, part, part2, part3);
             kb_scalar_init0<<<1, NSB, 0, s>>>(P->st, part, part2, P->pc ? nullptr : part3, nrb0, kpad, ca, h, 1);
             cudaGraph_t body = add_while(s, h);
             if (!P->pc) kb_final<<<grid(ntile, nrb0), NTB, 0, s>>>(D0, ca, P->x64, nullptr);
@@ -2145,9 +2236,7 @@ static void run_eager(mg_ctx* c, GraphPlan& P, int iters) {
     double* part3 = part2 + (size_t)P.ntile * nrb0 * G;
     const CallArgs* ca = P.args.as<CallArgs>();
     if (P.precision == MG_FP64) {
-        kb_init<0><<<grid(P.ntile, nrb0), NTB, 0, s>>>(D0, ca, 1.0 / P.op->dt, m0.F.as<double>(), c->pwm.J0, P.x64,
-                                                       P.r64, P.p64, P.q64, nullptr, D0.x, part, part2, part3,
-                                                       P.r32s, nullptr, nullptr, nullptr);
+        launch_init0(P, s, ca, 1.0 / P.op->dt, m0.F.as<double>(), c->pwm.J0, part, part2, part3);
         kb_scalar_init0<<<1, NSB, 0, s>>>(P.st, part, part2, part3, nrb0, kpad, ca, 0, 0);
         for (int it = 0; it < iters; ++it)
             capture_pcg_body<double>(P, s, P.x64, P.r64, P.p64, P.q64, D0.L64, ca, 0, 0, 0);

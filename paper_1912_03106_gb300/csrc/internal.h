@@ -106,6 +106,7 @@ struct MgDepth {
     int W = 0;
     DBuf L64, M64, L32, LD32, dinv64, dinv32;  // ELL values (W x n) and Jacobi data
     DBuf Llo32;  // L64 - L32 rounded to FP32: L32 + Llo32 carries L64 to about 2^-48
+    DBuf M32, Mlo32;  // the same two-part FP32 form of M64
     float lam = 0.0f;  // Gershgorin bound of the spectrum of D^-1 L (rounded up)
 };
 

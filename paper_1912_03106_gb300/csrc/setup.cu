@@ -161,7 +161,8 @@ __global__ void k_phase_loads(int64_t n, const int32_t* __restrict__ ptr, const 
 // ELL values of L = M/dt + K (and M) from the CSR values; padding entries are 0.
 __global__ void k_ell_values(int64_t nW, const int32_t* __restrict__ slot, const double* __restrict__ K,
                              const double* __restrict__ M, double inv_dt, double* __restrict__ L64,
-                             double* __restrict__ M64, float* __restrict__ L32, float* __restrict__ Llo32) {
+                             double* __restrict__ M64, float* __restrict__ L32, float* __restrict__ Llo32,
+                             float* __restrict__ M32, float* __restrict__ Mlo32) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nW) return;
     int32_t s = slot[q];
@@ -175,6 +176,9 @@ __global__ void k_ell_values(int64_t nW, const int32_t* __restrict__ slot, const
     const float hi = (float)l;
     L32[q] = hi;
     Llo32[q] = (float)(l - (double)hi);  // exact difference, rounded once
+    const float mh = (float)m;
+    M32[q] = mh;
+    Mlo32[q] = (float)(m - (double)mh);
 }
 
 __global__ void k_ell_diag(int64_t n, int W, const int32_t* __restrict__ col, const double* __restrict__ L64,
@@ -536,13 +540,15 @@ static MgDepth* build_depth(mg_ctx* c, int mesh, double dt) {
     d->M64.ensure(nW * sizeof(double));
     d->L32.ensure(nW * sizeof(float));
     d->Llo32.ensure(nW * sizeof(float));
+    d->M32.ensure(nW * sizeof(float));
+    d->Mlo32.ensure(nW * sizeof(float));
     d->LD32.ensure(nW * sizeof(float));
     d->dinv64.ensure(m.n * sizeof(double));
     d->dinv32.ensure(m.n * sizeof(float));
     cudaStream_t s = c->stream;
     k_ell_values<<<nblk(nW), 256, 0, s>>>(nW, m.ell_slot.as<int32_t>(), m.K.as<double>(), m.M.as<double>(), 1.0 / dt,
                                          d->L64.as<double>(), d->M64.as<double>(), d->L32.as<float>(),
-                                         d->Llo32.as<float>());
+                                         d->Llo32.as<float>(), d->M32.as<float>(), d->Mlo32.as<float>());
     k_ell_diag<<<nblk(m.n), 256, 0, s>>>(m.n, m.ell_W, m.ell_col.as<int32_t>(), d->L64.as<double>(),
                                         d->dinv64.as<double>(), d->dinv32.as<float>(), c->flag.as<int>());
     k_ell_scaled<<<nblk(nW), 256, 0, s>>>(nW, m.n, m.ell_col.as<int32_t>(), d->L64.as<double>(),

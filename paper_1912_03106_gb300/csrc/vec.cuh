@@ -134,6 +134,39 @@ __device__ __forceinline__ double f2d_int(float f) {
     return __longlong_as_double((long long)(e ? (sign | ex | mant) : sign));
 }
 
+// x split into two floats, x ~ h + l, by integer instructions: h is x with its
+// significand truncated to 24 bits (exact), l the remaining 29 bits truncated to
+// 24 (|x - h - l| <= 2^-47 |x|).  Magnitudes below the float range give h = l = 0
+// (their products sit far below the sums they enter); infinities and NaNs give
+// h = x as a float (NaN stays NaN) and l = 0, so poisoned inputs stay visible.
+__device__ __forceinline__ void split_d2f(double x, float& h, float& l) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7ffull);
+    l = 0.0f;
+    if (e == 0x7ff) {
+        h = __uint_as_float(sign | 0x7f800000u | ((u & 0xfffffffffffffull) ? 0x400000u : 0u));
+        return;
+    }
+    const int eh = e - 1023 + 127;
+    if (eh <= 0) {
+        h = 0.0f;
+        return;
+    }
+    if (eh >= 255) {  // beyond the float range
+        h = __uint_as_float(sign | 0x7f800000u);
+        return;
+    }
+    h = __uint_as_float(sign | ((unsigned)eh << 23) | (unsigned)((u >> 29) & 0x7fffffull));
+    const unsigned rem = (unsigned)(u & 0x1fffffffull);  // value rem * 2^(e - 1075)
+    if (!rem) return;
+    const int top = 31 - __clz(rem);  // leading one of rem, 0 .. 28
+    const int el = top + e - 1075 + 127;
+    if (el <= 0) return;
+    const unsigned frac = top >= 23 ? (rem >> (top - 23)) & 0x7fffffu : (rem << (23 - top)) & 0x7fffffu;
+    l = __uint_as_float(sign | ((unsigned)el << 23) | frac);
+}
+
 // Double-float accumulator of products in FP32 arithmetic: hi holds the running
 // sum of the rounded leading products (each addition's rounding error is kept by
 // two-sum), lo the FP32 sum of those errors, of the products' own FMA error terms
@@ -149,6 +182,16 @@ struct DfAcc {
         const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));  // hi + p = s + err
         hi = s;
         lo = __fmaf_rn(al, z, __fadd_rn(lo, __fadd_rn(err, pe)));
+    }
+    // += (ah + al) (xh + xl), dropping al * xl
+    __device__ __forceinline__ void add(float ah, float al, float xh, float xl) {
+        const float p = __fmul_rn(ah, xh);
+        const float pe = __fmaf_rn(ah, xh, -p);  // ah * xh = p + pe exactly
+        const float s = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));  // hi + p = s + err
+        hi = s;
+        lo = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, __fadd_rn(lo, __fadd_rn(err, pe))));
     }
     __device__ __forceinline__ double value() const { return f2d_int(hi) + f2d_int(lo); }
 };
