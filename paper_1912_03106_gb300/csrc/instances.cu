@@ -16,13 +16,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <condition_variable>
-#include <mutex>
-#include <numeric>
-#include <thread>
 #include <vector>
 
 #include "internal.h"
+#include "job_sched.h"
 
 namespace {
 
@@ -58,66 +55,23 @@ extern "C" mg_status mg_batch_solve(mg_ctx* const* ctxs, int n, const int64_t* N
         budget = (size_t)work_budget;
     }
     std::vector<size_t> est(n, 0);
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    if (budget) {
+    if (budget)
         for (int i = 0; i < n; ++i) {
             int64_t b = 0;
             if (mg_solve_work_bytes(ctxs[i], N[i], &opts[i], &b) == MG_OK) est[i] = (size_t)b;
         }
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return est[a] > est[b]; });
-    }
-    std::vector<mg_status> st(n, MG_OK);
-    std::vector<int> retry;
-    std::mutex mu;
-    std::condition_variable cv;
-    size_t in_use = 0;
-    int running = 0, next = 0;
-    auto worker = [&]() {
-        for (;;) {
-            std::unique_lock<std::mutex> lk(mu);
-            if (next >= n) return;
-            const int i = order[next++];
-            if (budget) cv.wait(lk, [&] { return running == 0 || in_use + est[i] <= budget; });
-            in_use += est[i];
-            ++running;
-            lk.unlock();
-            mg_stats* si = stats ? &stats[i] : nullptr;
-            st[i] = solve_one(ctxs[i], N[i], T[i], a0[i], out[i], opts[i], si);
-            if (budget) mg_release_work(ctxs[i]);
-            lk.lock();
-            in_use -= est[i];
-            --running;
-            if (budget && st[i] == MG_ENOMEM) retry.push_back(i);
-            lk.unlock();
-            cv.notify_all();
-        }
-    };
-    const int nt = max_threads == 0 ? n : std::min(n, max_threads);
-    std::vector<std::thread> pool;
-    pool.reserve(nt);
-    try {
-        for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
-    } catch (...) {
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            next = n;  // no further instance starts
-        }
-        cv.notify_all();
-        for (auto& th : pool) th.join();
-        return MG_ENOMEM;
-    }
-    for (auto& th : pool) th.join();
-    // instances that ran out of memory next to others, now alone
-    for (int i : retry) {
-        mg_stats* si = stats ? &stats[i] : nullptr;
-        st[i] = solve_one(ctxs[i], N[i], T[i], a0[i], out[i], opts[i], si);
-        mg_release_work(ctxs[i]);
-    }
+    std::vector<int> st;
+    const bool started = mgsched::run_jobs(
+        n, est, budget, max_threads,
+        [&](int i) {
+            return (int)solve_one(ctxs[i], N[i], T[i], a0[i], out[i], opts[i], stats ? &stats[i] : nullptr);
+        },
+        [&](int i) { mg_release_work(ctxs[i]); }, st, (int)MG_ENOMEM);
+    if (!started) return MG_ENOMEM;
     mg_status worst = MG_OK;
     for (int i = 0; i < n; ++i) {
-        if (status) status[i] = st[i];
-        if (st[i] != MG_OK && (worst == MG_OK || st[i] < worst)) worst = st[i];
+        if (status) status[i] = (mg_status)st[i];
+        if (st[i] != MG_OK && (worst == MG_OK || st[i] < worst)) worst = (mg_status)st[i];
     }
     return worst;
 }
