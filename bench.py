@@ -98,20 +98,25 @@ def csrc_sha1() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per batched-step launch from the committed ncu summary, or None if
-    the summary is missing or was taken on other sources."""
+def last_traffic_capture():
+    """The committed ncu summary's DRAM bytes per batched-step launch and the hash of
+    the sources it was taken on, or None if the summary is missing."""
     try:
         fields = {}
         for line in open(TRAFFIC_FILE):
             if ":" in line and line.strip().startswith(("csrc_sha1", "traffic_bytes_per_launch")):
                 k, v = line.strip().split(":", 1)
-                fields[k.strip()] = v.strip()
-        if fields.get("csrc_sha1") == csrc_sha1():
-            return float(fields["traffic_bytes_per_launch"])
+                fields.setdefault(k.strip(), v.strip())
+        return {"bytes_per_launch": float(fields["traffic_bytes_per_launch"]), "csrc_sha1": fields["csrc_sha1"]}
     except (OSError, KeyError, ValueError):
-        pass
-    return None
+        return None
+
+
+def measured_traffic():
+    """DRAM bytes per batched-step launch from the committed ncu summary, or None if
+    the summary is missing or was taken on other sources."""
+    cap = last_traffic_capture()
+    return cap["bytes_per_launch"] if cap and cap["csrc_sha1"] == csrc_sha1() else None
 
 
 def parse():
@@ -798,6 +803,8 @@ def roofline(ctx, ids, w, stream):
             "achieved": achieved, "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
             "achieved_all_passes": achieved_all, "frac_all_passes": achieved_all / peak,
             "traffic": measured_traffic() if (lvl == 2 and k == 256 and w.precision == 0) else None,
+            "traffic_last_capture": (dict(last_traffic_capture() or {}, sources_now=csrc_sha1())
+                                     if (lvl == 2 and k == 256 and w.precision == 0) else None),
             "launch_ms": t * 1e3, "pcg_iters_per_column": it_per_col,
             "algorithmic_bytes_per_launch": bytes_survey, "all_pass_bytes_per_launch": bytes_all,
             "l2_resident": resident}
