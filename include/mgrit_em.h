@@ -412,12 +412,16 @@ mg_status mg_joule_losses(mg_ctx* ctx, int level, int64_t N, double T, const dou
 /* Temporal coarsening plan (Sec. 4.1's heuristic, no GPU work): from measured
  * times ms_list[i] of one batched step of k_list[i] columns, the batch width k*
  * is the smallest one whose throughput (columns per ms) is within 90 % of the
- * best; the first coarsening factor m0 is the largest power of two dividing N
- * with N / m0 >= k* (at least 2), every further level coarsens by 2 while it
+ * best (the counterpart of Sec. 4.1's number of processors); the first
+ * coarsening factor m0 is the largest divisor of N (at least 2) with N / m0 >= k*,
+ * so that the second grid has about one interval per column of the widest
+ * efficient batch; every further level coarsens by coarse_m (0: 2, the factor of
+ * Sec. 4.1's worked example; the paper's runs use 4) while N stays divisible and
  * keeps at least 2 intervals and levels < max_levels.  Writes *levels_out and
- * m_out[0 .. levels-2] (the rest 0).  MG_EINVAL for odd N or bad input. */
+ * m_out[0 .. levels-2] (the rest 0).  MG_EINVAL if no divisor qualifies or for
+ * bad input. */
 mg_status mg_choose_levels(const double* k_list, const double* ms_list, int nk, int64_t N, int max_levels,
-                           int* levels_out, int* m_out);
+                           int coarse_m, int* levels_out, int* m_out);
 
 /* Measures batched-step times on mesh fine_level for 16, 32, ..., 1024 columns
  * (at most N/2) and applies mg_choose_levels; then runs 4 MGRIT iterations (from

@@ -327,16 +327,16 @@ def mg_smoother_weights(lam, nu, solver=None):
     return [w[i] for i in range(nu)]
 
 
-def mg_choose_levels(k_list, ms_list, N, max_levels=5):
-    """Sec. 4.1's coarsening heuristic on measured step times (host only).
-    Returns (levels, [m_0, ..., m_{levels-2}])."""
+def mg_choose_levels(k_list, ms_list, N, max_levels=5, coarse_m=0):
+    """Sec. 4.1's coarsening heuristic on measured step times (host only); coarse_m
+    is the factor below the first level (0: 2).  Returns (levels, [m_0, ..., m_{levels-2}])."""
     lib = L.load()
     nk = len(k_list)
     ks = (C.c_double * nk)(*k_list)
     ts = (C.c_double * nk)(*ms_list)
     lv = C.c_int(0)
     m = (C.c_int * 8)()
-    rc = lib.mg_choose_levels(ks, ts, nk, N, max_levels, C.byref(lv), m)
+    rc = lib.mg_choose_levels(ks, ts, nk, N, max_levels, coarse_m, C.byref(lv), m)
     if rc != L.MG_OK:
         raise L.MgError(rc, "mg_choose_levels: bad input")
     return lv.value, [m[i] for i in range(lv.value - 1)]

@@ -182,15 +182,18 @@ extern "C" mg_status mg_autotune(mg_ctx* c, int level, int64_t N, double T, int 
 // ------------------------------------------------------------------ temporal coarsening plan
 //
 // Sec. 4.1 chooses a large first coarsening factor so that the second time grid
-// has one point per processor, and factor 2 on the coarser grids.  On one GPU the
+// has one point per processor, and a small factor on the coarser grids (2 in its
+// worked example, 4 in the runs of Secs. 4.2 and 5).  On one GPU the
 // counterpart of "one point per processor" is the batch width from which a
 // batched step stops gaining throughput: the first factor makes the finest
 // relaxation batches that wide.
 
 extern "C" mg_status mg_choose_levels(const double* k_list, const double* ms_list, int nk, int64_t N, int max_levels,
-                                      int* levels_out, int* m_out) {
-    if (!k_list || !ms_list || nk <= 0 || N < 2 || max_levels < 2 || max_levels > 8 || !levels_out || !m_out)
+                                      int coarse_m, int* levels_out, int* m_out) {
+    if (!k_list || !ms_list || nk <= 0 || N < 2 || max_levels < 2 || max_levels > 8 || coarse_m < 0 ||
+        coarse_m == 1 || !levels_out || !m_out)
         return MG_EINVAL;
+    const int64_t cm = coarse_m ? coarse_m : 2;
     double best = 0.0;
     for (int i = 0; i < nk; ++i) {
         if (!(k_list[i] >= 1.0) || !(ms_list[i] > 0.0)) return MG_EINVAL;
@@ -199,16 +202,20 @@ extern "C" mg_status mg_choose_levels(const double* k_list, const double* ms_lis
     double kstar = 0.0;
     for (int i = 0; i < nk; ++i)
         if (k_list[i] / ms_list[i] >= 0.9 * best && (kstar == 0.0 || k_list[i] < kstar)) kstar = k_list[i];
-    // first factor: the largest power of two dividing N with N / m0 >= kstar (at least 2)
-    int64_t m0 = 2;
-    while (N % (m0 * 2) == 0 && (double)(N / (m0 * 2)) >= kstar) m0 *= 2;
-    if (N % m0) return MG_EINVAL;  // N odd
+    // first factor: the largest divisor of N with N / m0 >= kstar (at least 2)
+    int64_t m0 = 0;
+    for (int64_t m = std::min<int64_t>(N / 2, (int64_t)(N / std::max(1.0, kstar))); m >= 2; --m)
+        if (N % m == 0 && (double)(N / m) >= kstar) {
+            m0 = m;
+            break;
+        }
+    if (!m0) return MG_EINVAL;
     int levels = 2;
     m_out[0] = (int)m0;
     int64_t Nl = N / m0;
-    while (levels < max_levels && Nl % 2 == 0 && Nl / 2 >= 2) {
-        m_out[levels - 1] = 2;
-        Nl /= 2;
+    while (levels < max_levels && Nl % cm == 0 && Nl / cm >= 2) {
+        m_out[levels - 1] = (int)cm;
+        Nl /= cm;
         ++levels;
     }
     for (int l = levels - 1; l < 8; ++l) m_out[l] = 0;
@@ -276,7 +283,7 @@ extern "C" mg_status mg_plan_levels(mg_ctx* c, int fine_level, int coarse_level,
                 ms.push_back(time_step(A.fine, A.N, k));
             }
             int levels = 0, m[8] = {};
-            if (mg_choose_levels(ks.data(), ms.data(), (int)ks.size(), A.N, std::max(2, A.max_levels), &levels, m) !=
+            if (mg_choose_levels(ks.data(), ms.data(), (int)ks.size(), A.N, std::max(2, A.max_levels), 0, &levels, m) !=
                 MG_OK)
                 mg_fail(MG_EINVAL, "mg_plan_levels: N has no power-of-two coarsening");
             // candidate hierarchies: the heuristic's and fixed factors that divide N; each

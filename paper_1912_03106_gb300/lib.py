@@ -126,7 +126,7 @@ _SIGNATURES = {
     "mg_sequential_host": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P, C.POINTER(mg_solver_opts),
                                      C.POINTER(mg_stats)]),
     "mg_smoother_weights": (C.c_int, [C.POINTER(mg_solver_opts), _D, C.c_int, C.POINTER(C.c_float)]),
-    "mg_choose_levels": (C.c_int, [C.POINTER(_D), C.POINTER(_D), C.c_int, _I64, C.c_int, C.POINTER(C.c_int),
+    "mg_choose_levels": (C.c_int, [C.POINTER(_D), C.POINTER(_D), C.c_int, _I64, C.c_int, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_int)]),
     "mg_plan_levels": (C.c_int, [_P, C.c_int, C.c_int, _I64, _D, C.c_int, C.POINTER(mg_opts), C.POINTER(_D)]),
     "mg_joule_losses": (C.c_int, [_P, C.c_int, _I64, _D, _P, _P]),

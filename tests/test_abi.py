@@ -175,8 +175,30 @@ def test_choose_levels_heuristic():
     # the coarsest level keeps at least 2 intervals
     levels, m = api.mg_choose_levels([16], [1.0], 64, max_levels=8)
     assert m[0] == 4 and 64 // 4 // (2 ** (levels - 2)) >= 2
-    with pytest.raises(api.L.MgError):
-        api.mg_choose_levels([16], [1.0], 63)
+    # any divisor, not only powers of two: 63 = 3 x 21 gives 21 intervals >= 16
+    levels, m = api.mg_choose_levels([16], [1.0], 63, max_levels=2)
+    assert levels == 2 and m == [3]
+    with pytest.raises(api.L.MgError):  # a prime number of intervals has no qualifying factor
+        api.mg_choose_levels([16], [1.0], 61)
+
+
+def test_choose_levels_reproduces_the_printed_examples():
+    """Every temporal coarsening choice the paper prints (tests/golden/
+    temporal_coarsening_examples.txt, each with its source): with step times that
+    grow linearly from `processors` columns on, the batch width at which throughput
+    stops growing is the processor count, and the heuristic gives the paper's
+    factors."""
+    from paper_1912_03106_gb300 import api
+
+    path = os.path.join(ROOT, "tests", "golden", "temporal_coarsening_examples.txt")
+    rows = [ln.split(None, 5) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 2
+    for n, p, lv, cm, want, _src in rows:
+        p = int(p)
+        ks = [p // 4, p // 2, p, 2 * p, 4 * p]
+        ms = [1.0, 1.0, 1.0, 2.0, 4.0]  # flat below p, linear above: throughput peaks at p
+        levels, m = api.mg_choose_levels(ks, ms, int(n), max_levels=int(lv), coarse_m=int(cm))
+        assert levels == int(lv) and m == [int(x) for x in want.split(",")], (n, p, levels, m)
 
 
 def test_choose_levels_reproduces_the_worked_example():
